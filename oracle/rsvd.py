@@ -1,0 +1,91 @@
+"""Algorithms on top of the march: power iteration and block randomized SVD (oracle).
+
+App. A: the action w = R_y^H R_y f (App. A Eq. (iteration)) comes from one
+direct and one adjoint run.  With f_n = w_{n-1} the iterate converges to the
+leading forcing mode (App. A Eq. (powerMethod)) and the gain is estimated by
+sigma_n = sqrt(||f_n|| / ||f_{n-1}||) (App. A Eq. (tildeSig)); the error falls
+by (sigma_2 / sigma_1)^2 per iteration.  Normalising per frequency on the
+Fourier coefficients replaces a temporal filter (Sec. 2.3).
+
+The block form runs k test vectors per frequency at once (the randomized SVD
+the paper cites in Sec. 1): Y = R Omega; q times {Q = qr(Y); Z = R^H Q;
+Q = qr(Z); Y = R Q}; Q = qr(Y); W = R^H Q; then B = W^H = Q^H R and its SVD
+B = U_s S V^H give gains S, response modes Q U_s and forcing modes V
+(Sec. 2.1: R_y = U Sigma V^H).
+
+`march_direct(block)` / `march_adjoint(block)` map [n_omega][k][n] blocks to
+[n_omega][k][n] blocks.  `instances` lists (offset, size) of independent
+diagonal blocks of a batched operator; each gets its own QR and SVD.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def qr_positive(y):
+    """Thin QR of y (n x k) with a positive real diagonal in R (unique form)."""
+    q, r = np.linalg.qr(y)
+    d = np.diag(r)
+    ph = np.where(np.abs(d) > 0, d / np.abs(d), 1.0)
+    return q * ph[None, :], ph.conj()[:, None] * r
+
+
+def orthonormalize(block, instances, real_rows=()):
+    out = np.empty_like(block)
+    for j in range(block.shape[0]):
+        for off, size in instances:
+            y = block[j, :, off:off + size].T
+            if j in real_rows:
+                y = y.real
+            q, _ = qr_positive(y)
+            out[j, :, off:off + size] = q.T
+    return out
+
+
+def power_iteration(march_direct, march_adjoint, f0, n_iter):
+    """Power iteration per frequency with per-frequency normalisation (k = 1 block).
+
+    Returns (gain estimates [n_iter][n_omega], last forcing f_n [n_omega][1][n]).
+    """
+    f = f0 / np.linalg.norm(f0, axis=(1, 2), keepdims=True)
+    hist = []
+    for _ in range(n_iter):
+        w = march_adjoint(march_direct(f))
+        nw = np.linalg.norm(w, axis=(1, 2))              # ||f_{n+1}|| with ||f_n|| = 1
+        hist.append(np.sqrt(nw))
+        f = w / nw[:, None, None]
+    return np.array(hist), f
+
+
+def block_rsvd(march_direct, march_adjoint, omega_block, n_power_iter, n_modes,
+               instances=None, real_rows=()):
+    """Randomized SVD of R(w_j) for every frequency; returns (gains, V, U).
+
+    gains [n_inst][n_omega][n_modes]; V, U [n_inst][n_omega][n_modes][n_i] lists.
+    """
+    nom, kk, n = omega_block.shape
+    inst = instances or [(0, n)]
+    y = march_direct(omega_block)
+    for _ in range(n_power_iter):
+        q = orthonormalize(y, inst, real_rows)
+        z = march_adjoint(q)
+        q = orthonormalize(z, inst, real_rows)
+        y = march_direct(q)
+    q = orthonormalize(y, inst, real_rows)
+    w = march_adjoint(q)
+    gains = np.zeros((len(inst), nom, n_modes))
+    vmodes, umodes = [], []
+    for i, (off, size) in enumerate(inst):
+        vi, ui = [], []
+        for j in range(nom):
+            qj = q[j, :, off:off + size].T                # n x k
+            bj = w[j, :, off:off + size].conj()           # k x n  = Q^H R
+            if j in real_rows:
+                bj = bj.real
+            us, s, vh = np.linalg.svd(bj, full_matrices=False)
+            gains[i, j] = s[:n_modes]
+            vi.append(vh[:n_modes].conj())                # forcing modes, rows
+            ui.append((qj @ us[:, :n_modes]).T)           # response modes, rows
+        vmodes.append(np.array(vi))
+        umodes.append(np.array(ui))
+    return gains, vmodes, umodes
