@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark: resolvent actions/s of the batched randomized-SVD time march.
+
+One step = one full randomized SVD of the workload (every direct and adjoint
+march plus the per-frequency QR / SVD glue) through rsv_gains_modes.  One
+resolvent action = one test vector x one frequency through one march.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank marches its own
+independent copy of the workload (frequency / test-vector blocks are
+independent problems), so the job is weak-scaled with no data-path
+collective; the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "resolvent actions/s (test vectors x freqs) at <=1e-4 gain error"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def marches_per_step(w) -> int:
+    return 2 * w.n_power_iter + 2
+
+
+def n_instances(w) -> int:
+    return len(w.system.n) if type(w.system).__name__ == "GL1D" else 1
+
+
+def actions_per_step(w) -> int:
+    return marches_per_step(w) * w.k * w.n_omega * n_instances(w)
+
+
+def workload(name: str):
+    return W.ALL[name]()
+
+
+def default_precision(name: str) -> str:
+    return "fp64" if name == "c1" else "fp32"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (also exercised by the CPU gloo tests)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def rank_seed_offset(rank: int) -> int:
+    """Each rank marches an independent test block (weak scaling)."""
+    return 1000 * rank
+
+
+def max_over_ranks(value: float, group=None, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds_max: float) -> float:
+    return units_per_rank * world / seconds_max
+
+
+# ---------------------------------------------------------------------------
+# per-kernel roofline model
+# ---------------------------------------------------------------------------
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "bf16_tflops": d.get("bf16_tflops", 1900.0),
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", 1700.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+def kernel_model(cat: str, w, prec: str, tile: int, launches: int, ms_total: float, rows: int):
+    """Algorithmic work per launch of the dominant kernel category (see design notes)."""
+    ce = 16 if prec == "fp64" else 8                    # complex coefficient bytes
+    se = (8 if prec == "fp64" else 4) * (1 if w.real_state else 2)
+    peaks = load_peaks()
+    avg_s = ms_total / max(launches, 1) / 1e3
+    if cat == "synthesis":
+        # read fhat once per tile, write 2S+1 forcing rows
+        b = w.n_omega * rows * ce + (2 * tile + 1) * rows * se
+    elif cat == "analysis":
+        # read S snapshots, read+write FP64 accumulators
+        b = tile * rows * se + 2 * w.n_omega * rows * 16
+    elif cat == "march":
+        # per tile: forcing rows in, snapshots out, state in/out
+        b = (2 * tile + 1) * rows * se + tile * rows * se + 2 * rows * se
+    else:
+        b = 2 * w.n_omega * rows * ce
+    achieved = b / avg_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": cat,
+            "bytes_per_launch": b, "avg_launch_ms": avg_s * 1e3, "peak_src": peaks["src"]}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample, in a subprocess with one thread
+# ---------------------------------------------------------------------------
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle import frequencies, march, operators
+w = W.ALL[{name!r}]()
+g = frequencies.make_grid(w.omegas, w.dt)
+kind = type(w.system).__name__
+a = (W.hermite_gl_matrix(w.system) if kind == "Dense" else
+     operators.gl1d(w.system) if kind == "GL1D" else
+     operators.adr2d(w.system) if kind == "ADR2D" else operators.adv3d(w.system))
+fh = W.test_block(w)
+total, first, forced = march.schedule(g, w.variant, w.n_transient_windows, w.tail_steps)
+steps = min({steps}, total)
+t0 = time.perf_counter()
+march.march(a, g, fh, variant=w.variant, n_trans=w.n_transient_windows, tail_steps=w.tail_steps,
+            real_state=w.real_state, stop_after=steps)
+dt = time.perf_counter() - t0
+print(json.dumps({{"seconds": dt, "steps": steps, "total_steps": int(total), "first": int(first)}}))
+"""
+
+
+def cpu_baseline(name: str, target_seconds: float = 15.0):
+    w = workload(name)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    probe = 200
+    r = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, name=name, steps=probe)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    per_step = d["seconds"] / d["steps"]
+    steps = max(probe, min(d["total_steps"], int(target_seconds / per_step)))
+    if steps > probe:
+        r = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, name=name, steps=steps)],
+                           capture_output=True, text=True, env=env, timeout=900)
+        if r.returncode != 0:
+            return {"value": None, "error": r.stderr[-400:]}
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        per_step = d["seconds"] / d["steps"]
+    # one march = total_steps steps and yields k * n_omega (* instances) actions
+    march_s = per_step * d["total_steps"]
+    actions = w.k * w.n_omega * n_instances(w)
+    return {"value": actions / march_s, "unit": "actions/s", "cores": 1, "kind": "oracle",
+            "sample": f"{d['steps']} of the {d['total_steps']} steps of one direct march of {w.name} "
+                      f"(FP64 numpy oracle, one thread), extrapolated to the full march",
+            "seconds": d["seconds"]}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2008_10904_gb300 import build as B
+    from paper_2008_10904_gb300 import rsv
+
+    if rank == 0 or ws == 1:
+        B.build()
+    if ws > 1:
+        dist.barrier()
+    rsv.load()
+    name = args.workload
+    w = workload(name)
+    prec_name = args.precision or default_precision(name)
+    prec = rsv.RSV_PREC_FP64 if prec_name == "fp64" else rsv.RSV_PREC_FP32
+    cdt = torch.complex128 if prec_name == "fp64" else torch.complex64
+    dense = W.hermite_gl_matrix(w.system) if type(w.system).__name__ == "Dense" else None
+    stream = torch.cuda.current_stream()
+    op = rsv.create_for_workload(w, prec, stream=stream.cuda_stream, dense_matrix=dense)
+    n_t, h = rsv.rsv_set_frequencies(op, w.omegas)
+    opts = rsv.march_opts_for(w, tile_steps=args.tile)
+    omega_host = W.test_block(w, seed_offset=rank_seed_offset(rank))
+    omega_dev = torch.from_numpy(omega_host).to(device="cuda", dtype=cdt)
+    ninst = n_instances(w)
+    gains = np.zeros((ninst, w.n_omega, w.n_modes))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        rsv.rsv_gains_modes(op, omega_dev, w.k, w.n_power_iter, w.n_modes, gains, **opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # timed region: device-resident inputs, L2 flushed between steps (outside the events)
+    sampler = ClockSampler(local)
+    sampler.start()
+    rsv.rsv_profile_reset(op)
+    rsv.rsv_profile_enable(op, True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    rsv.rsv_profile_enable(op, False)
+    clocks = sampler.stop()
+    prof = {c: rsv.rsv_profile_read(op, i) for i, c in enumerate(rsv.PROFILE_CATEGORIES)}
+    sec_max = max_over_ranks(total_ms / 1e3, device="cuda")
+    value = job_throughput(actions_per_step(w) * args.steps, ws, sec_max)
+    gains_timed = gains.copy()
+
+    # end to end through the public API: pinned host test block in, gains on the host out
+    pinned = torch.from_numpy(omega_host.astype(np.complex128 if prec_name == "fp64" else np.complex64)).pin_memory()
+    h2d = pinned.numel() * pinned.element_size()
+    d2h = gains.nbytes
+    e2e_ms = 0.0
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        omega_dev.copy_(pinned, non_blocking=True)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_sec = max_over_ranks(e2e_ms / 1e3, device="cuda")
+    e2e_value = job_throughput(actions_per_step(w) * max(1, args.steps), ws, e2e_sec)
+
+    # accuracy: the timed path's gains against the FP64 path (itself parity-tested against the oracle)
+    acc = None
+    if prec_name != "fp64" and not args.skip_accuracy:
+        op64 = rsv.create_for_workload(w, rsv.RSV_PREC_FP64, stream=stream.cuda_stream, dense_matrix=dense)
+        g64 = np.zeros_like(gains)
+        rsv.rsv_gains_modes(op64, omega_dev.to(torch.complex128), w.k, w.n_power_iter, w.n_modes, g64, **opts)
+        rsv.rsv_destroy_operator(op64)
+        acc = {"gain_rel_err_max": float(np.max(np.abs(gains_timed - g64) / np.abs(g64))),
+               "vs": "FP64 GPU path (parity-tested against the FP64 oracle to 1e-10)"}
+    elif prec_name == "fp64":
+        acc = {"gain_rel_err_max": 0.0, "vs": "FP64 path itself (parity-tested against the oracle to 1e-10)"}
+
+    dom = max(prof, key=lambda c: prof[c][1])
+    rows = w.k * w.n
+    tile = args.tile or 256
+    roof = kernel_model(dom, w, prec_name, tile, prof[dom][0], prof[dom][1], rows)
+    launches = sum(v[0] for v in prof.values())
+    steps_per_march = {"ssrm": (w.n_transient_windows + 1) * n_t, "trm": n_t + w.tail_steps}[w.variant]
+    out = {
+        "metric": METRIC, "value": value, "unit": "actions/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec_name == "fp64" else "f32",
+        "data": "synthetic (seeded Gaussian test vectors, workload of the config)",
+        "config": {"workload": w.name, "n": w.n, "k": w.k, "n_omega": w.n_omega, "variant": w.variant,
+                   "steps_per_window": n_t, "h": h, "steps_per_march": steps_per_march,
+                   "marches_per_step": marches_per_step(w), "actions_per_step": actions_per_step(w),
+                   "power_iterations": w.n_power_iter, "precision": prec_name,
+                   "l2": "flushed between steps (512 MiB write outside the timed events)",
+                   "parallelism": f"independent replicas x{ws}"},
+        "e2e": {"value": e2e_value, "unit": "actions/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "kernel_ms": {c: {"launches": v[0], "ms": v[1]} for c, v in prof.items()},
+        "roofline": roof,
+        "clocks": clocks,
+        "accuracy": acc,
+    }
+    rsv.rsv_destroy_operator(op)
+    if rank == 0:
+        if not args.no_cpu_baseline and ws == 1:
+            out["cpu_baseline"] = cpu_baseline(name)
+        else:
+            out["cpu_baseline"] = None
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    name = args.workload
+    w = workload(name)
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(max(1, args.steps)):
+        last = cpu_baseline(name, target_seconds=args.ref_seconds)
+        if last.get("value"):
+            vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals) if vals else None
+    out = {"metric": METRIC, "value": v, "unit": "actions/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": w.name, "n": w.n, "k": w.k, "n_omega": w.n_omega, "variant": w.variant},
+           "cpu_baseline": dict(last or {}, value=v),
+           "e2e": {"value": v, "unit": "actions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(W.ALL), default="c1")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default=None)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

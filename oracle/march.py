@@ -64,10 +64,11 @@ def schedule(grid, variant, n_trans=0, tail_steps=0):
 
 
 def march(a, grid, fhat, *, variant="ssrm", n_trans=0, tail_steps=0, adjoint=False,
-          real_state=False, return_state=False):
+          real_state=False, return_state=False, stop_after=None):
     """Direct (adjoint=False) or adjoint run; returns yhat [n_omega][k][n].
 
     `a` is the system matrix (sparse or dense); the adjoint run uses a^H.
+    `stop_after` ends the march early (for timing a bounded sample only).
     """
     op = a.conj().T.tocsr() if (adjoint and hasattr(a, "tocsr")) else (a.conj().T if adjoint else a)
     om = -grid.omegas if adjoint else grid.omegas
@@ -79,7 +80,7 @@ def march(a, grid, fhat, *, variant="ssrm", n_trans=0, tail_steps=0, adjoint=Fal
     u = np.zeros((n, kk), dtype=dtype)
     acc = np.zeros((nom, kk, n), dtype=np.complex128)
     zero = np.zeros((n, kk), dtype=dtype)
-    for step in range(total):
+    for step in range(total if stop_after is None else min(total, stop_after)):
         t = step * h
         if step >= first:
             acc += np.exp(-1j * om * t)[:, None, None] * u.T[None, :, :]

@@ -1,0 +1,190 @@
+// Forcing synthesis and response analysis over one time tile.
+//
+// Synthesis (Sec. 2.3, Eq. (forceFseries), sign flipped to exp(+i w t)):
+//   F[tau][r] = sum_j fhat[j][r] exp(i sgn w_j t_tau),  t_tau = (2 n0 + tau) h / 2,
+// for the tile's 2 S + 1 stage times (step starts and midpoints).  For a real
+// state the forcing is sum_j c_j Re(fhat_j exp(i w_j t)), c_j = 1 at w = 0, else 2.
+//
+// Analysis (Sec. 2.1, Eq. (fourier), rectangle rule over the window):
+//   acc[j][r] += sum_s Y[s][r] exp(-i sgn w_j t_s),  t_s = (n0 + s) h.
+//
+// Both are contractions over a short dimension (frequencies or tile steps)
+// that stream one long dimension r (state rows): each thread owns one row and
+// keeps a chunk of outputs in registers; the exact twiddles exp(i pi q / 2N_T)
+// (integer phase index q) are staged in shared memory per block.  Products
+// and in-tile sums run in the element precision R; in-tile partial sums are
+// folded into FP64 registers every 64 steps and then added to the FP64
+// accumulator array once per tile.
+#include "rsv_internal.h"
+
+namespace rsv {
+namespace {
+
+constexpr int kTPB = 128;
+constexpr int kTauChunk = 8;
+constexpr int kOmChunk = 8;
+constexpr int kSChunk = 64;
+
+template <typename R, bool REAL>
+__global__ void __launch_bounds__(kTPB) synth_kernel(TileGeom g, const cpx<R>* __restrict__ fhat,
+                                                     const cpx<R>* __restrict__ tw,
+                                                     const int64_t* __restrict__ pj,
+                                                     const float* __restrict__ cw, void* __restrict__ Fout) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);  // [kTauChunk][n_omega]
+  const int n_tau = 2 * g.steps + 1;
+  const int tau0 = blockIdx.y * kTauChunk;
+  const int nt = min(kTauChunk, n_tau - tau0);
+  for (int e = threadIdx.x; e < nt * g.n_omega; e += blockDim.x) {
+    const int t = e / g.n_omega, j = e - t * g.n_omega;
+    const int64_t q = phase_index(g.sgn * pj[j], 2 * g.n0 + tau0 + t, g.m4);
+    cpx<R> v = tw[q];
+    if (REAL) v = R(cw[j]) * v;
+    stw[t * g.n_omega + j] = v;
+  }
+  __syncthreads();
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.rows) return;
+  cpx<R> acc[kTauChunk];
+#pragma unroll
+  for (int t = 0; t < kTauChunk; ++t) acc[t] = mk<R>(0, 0);
+  for (int j = 0; j < g.n_omega; ++j) {
+    const cpx<R> x = fhat[(int64_t)j * g.coef_stride + r];
+#pragma unroll
+    for (int t = 0; t < kTauChunk; ++t) {
+      const cpx<R> w = stw[t * g.n_omega + j];
+      if (REAL) {
+        acc[t].re = fma(w.re, x.re, fma(-w.im, x.im, acc[t].re));
+      } else {
+        cfma(acc[t], w, x);
+      }
+    }
+  }
+  if (REAL) {
+    R* F = reinterpret_cast<R*>(Fout);
+    for (int t = 0; t < nt; ++t) F[(int64_t)(tau0 + t) * g.rows + r] = acc[t].re;
+  } else {
+    cpx<R>* F = reinterpret_cast<cpx<R>*>(Fout);
+    for (int t = 0; t < nt; ++t) F[(int64_t)(tau0 + t) * g.rows + r] = acc[t];
+  }
+}
+
+template <typename R, bool REAL>
+__global__ void __launch_bounds__(kTPB) analysis_kernel(TileGeom g, const void* __restrict__ Yin, int s0, int s1,
+                                                        const cpx<R>* __restrict__ tw,
+                                                        const int64_t* __restrict__ pj,
+                                                        cpx<double>* __restrict__ acc, int64_t acc_stride) {
+  __shared__ cpx<R> stw[kSChunk][kOmChunk];
+  const int j0 = blockIdx.y * kOmChunk;
+  const int nj = min(kOmChunk, g.n_omega - j0);
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  cpx<double> a64[kOmChunk];
+#pragma unroll
+  for (int jj = 0; jj < kOmChunk; ++jj) a64[jj] = mk<double>(0, 0);
+  for (int sc = s0; sc < s1; sc += kSChunk) {
+    const int ns = min(kSChunk, s1 - sc);
+    __syncthreads();
+    for (int e = threadIdx.x; e < ns * kOmChunk; e += blockDim.x) {
+      const int s = e / kOmChunk, jj = e - s * kOmChunk;
+      cpx<R> v = mk<R>(0, 0);
+      if (jj < nj) v = tw[phase_index(g.sgn * pj[j0 + jj], 2 * (g.n0 + sc + s), g.m4)];
+      stw[s][jj] = v;
+    }
+    __syncthreads();
+    if (r < g.rows) {
+      cpx<R> a[kOmChunk];
+#pragma unroll
+      for (int jj = 0; jj < kOmChunk; ++jj) a[jj] = mk<R>(0, 0);
+      for (int s = 0; s < ns; ++s) {
+        cpx<R> y;
+        if (REAL) {
+          y = mk<R>(reinterpret_cast<const R*>(Yin)[(int64_t)(sc + s) * g.rows + r], R(0));
+        } else {
+          y = reinterpret_cast<const cpx<R>*>(Yin)[(int64_t)(sc + s) * g.rows + r];
+        }
+#pragma unroll
+        for (int jj = 0; jj < kOmChunk; ++jj) cfma_conj(a[jj], stw[s][jj], y);
+      }
+#pragma unroll
+      for (int jj = 0; jj < kOmChunk; ++jj) {
+        a64[jj].re += (double)a[jj].re;
+        a64[jj].im += (double)a[jj].im;
+      }
+    }
+  }
+  if (r >= g.rows) return;
+  for (int jj = 0; jj < nj; ++jj) {
+    cpx<double>* p = acc + (int64_t)(j0 + jj) * acc_stride + r;
+    cpx<double> v = *p;
+    v.re += a64[jj].re;
+    v.im += a64[jj].im;
+    *p = v;
+  }
+}
+
+template <typename R>
+__global__ void finish_kernel(const cpx<double>* __restrict__ acc, int64_t acc_stride, int n_omega, int64_t rows,
+                              double scale, cpx<R>* __restrict__ out, int64_t out_stride) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (r >= rows || j >= n_omega) return;
+  const cpx<double> v = acc[(int64_t)j * acc_stride + r];
+  out[(int64_t)j * out_stride + r] = mk<R>(R(v.re * scale), R(v.im * scale));
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_synth(const TileGeom& g, const void* fhat, const void* tw, const int64_t* pj, const float* cw,
+                         bool real_state, void* F, cudaStream_t st) {
+  const int n_tau = 2 * g.steps + 1;
+  dim3 grid((unsigned)((g.rows + kTPB - 1) / kTPB), (unsigned)((n_tau + kTauChunk - 1) / kTauChunk));
+  const size_t smem = sizeof(cpx<R>) * kTauChunk * g.n_omega;
+  if (real_state) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(synth_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    synth_kernel<R, true><<<grid, kTPB, smem, st>>>(g, (const cpx<R>*)fhat, (const cpx<R>*)tw, pj, cw, F);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(synth_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    synth_kernel<R, false><<<grid, kTPB, smem, st>>>(g, (const cpx<R>*)fhat, (const cpx<R>*)tw, pj, cw, F);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_analysis(const TileGeom& g, const void* Y, int s0, int s1, const void* tw, const int64_t* pj,
+                            bool real_state, cpx<double>* acc, int64_t acc_stride, cudaStream_t st) {
+  if (s1 <= s0) return cudaSuccess;
+  dim3 grid((unsigned)((g.rows + kTPB - 1) / kTPB), (unsigned)((g.n_omega + kOmChunk - 1) / kOmChunk));
+  if (real_state)
+    analysis_kernel<R, true><<<grid, kTPB, 0, st>>>(g, Y, s0, s1, (const cpx<R>*)tw, pj, acc, acc_stride);
+  else
+    analysis_kernel<R, false><<<grid, kTPB, 0, st>>>(g, Y, s0, s1, (const cpx<R>*)tw, pj, acc, acc_stride);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_finish(const cpx<double>* acc, int64_t acc_stride, int n_omega, int64_t rows, double scale,
+                          void* out, int64_t out_stride, cudaStream_t st) {
+  dim3 grid((unsigned)((rows + 255) / 256), (unsigned)n_omega);
+  finish_kernel<R><<<grid, 256, 0, st>>>(acc, acc_stride, n_omega, rows, scale, (cpx<R>*)out, out_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(p, 0, bytes, st); }
+
+template cudaError_t launch_synth<double>(const TileGeom&, const void*, const void*, const int64_t*, const float*,
+                                         bool, void*, cudaStream_t);
+template cudaError_t launch_synth<float>(const TileGeom&, const void*, const void*, const int64_t*, const float*,
+                                        bool, void*, cudaStream_t);
+template cudaError_t launch_analysis<double>(const TileGeom&, const void*, int, int, const void*, const int64_t*,
+                                            bool, cpx<double>*, int64_t, cudaStream_t);
+template cudaError_t launch_analysis<float>(const TileGeom&, const void*, int, int, const void*, const int64_t*,
+                                           bool, cpx<double>*, int64_t, cudaStream_t);
+template cudaError_t launch_finish<double>(const cpx<double>*, int64_t, int, int64_t, double, void*, int64_t,
+                                          cudaStream_t);
+template cudaError_t launch_finish<float>(const cpx<double>*, int64_t, int, int64_t, double, void*, int64_t,
+                                         cudaStream_t);
+
+}  // namespace rsv

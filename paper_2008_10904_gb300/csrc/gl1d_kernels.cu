@@ -1,0 +1,210 @@
+// RK4 march of 1-D three-point (tridiagonal) operators: the linearised
+// Ginzburg-Landau family of Sec. 3, Eq. (GL_timeDomain), discretised with
+// central differences, one or many independent instances.
+//
+// One CTA owns one (instance, test vector) pair for a whole time tile: the
+// state lives in registers (PPT points per thread), each RK4 stage
+// exchanges the stage input through shared memory (one barrier per stage,
+// two alternating buffers), and the forcing for the tile's 2S+1 stage times
+// is read from the synthesis tile F.  The state at the start of each
+// analysed step is written to the snapshot tile Y for the analysis kernel.
+//
+//   k1 = A u + f(t_n)
+//   k2 = A (u + h/2 k1) + f(t_n + h/2)
+//   k3 = A (u + h/2 k2) + f(t_n + h/2)
+//   k4 = A (u + h k3)   + f(t_n + h)
+//   u <- u + h/6 (k1 + 2 k2 + 2 k3 + k4)
+#include "rsv_internal.h"
+
+namespace rsv {
+namespace {
+
+template <typename R, int PPT>
+__global__ void __launch_bounds__(1024) gl1d_tile_kernel(Gl1dTile t, cpx<R>* __restrict__ u,
+                                                         const cpx<R>* __restrict__ F, cpx<R>* __restrict__ Y,
+                                                         double* __restrict__ norms, int* __restrict__ flag) {
+  extern __shared__ unsigned char smem_raw[];
+  const int inst = blockIdx.x;
+  const int v = blockIdx.y;
+  const int64_t off = t.inst_off[inst];
+  const int len = (int)(t.inst_off[inst + 1] - off);
+  const int ld = t.max_n + 2;
+  cpx<R>* sx = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][max_n + 2], zero halo at both ends
+  const cpx<R>* lo = reinterpret_cast<const cpx<R>*>(t.lo);
+  const cpx<R>* di = reinterpret_cast<const cpx<R>*>(t.di);
+  const cpx<R>* up = reinterpret_cast<const cpx<R>*>(t.up);
+  const cpx<R> zero = mk<R>(0, 0);
+  if (threadIdx.x == 0) {
+    sx[0] = zero;
+    sx[ld] = zero;
+    sx[len + 1] = zero;
+    sx[ld + len + 1] = zero;
+  }
+  const int64_t rows = (int64_t)t.kg * t.n;
+  const int64_t rbase = (int64_t)v * t.n + off;
+  cpx<R> cl[PPT], cd[PPT], cu[PPT], us[PPT];
+  bool ok[PPT];
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) {
+    const int i = threadIdx.x + m * blockDim.x;
+    ok[m] = i < len;
+    if (ok[m]) {
+      cl[m] = lo[off + i];
+      cd[m] = di[off + i];
+      cu[m] = up[off + i];
+      us[m] = u[rbase + i];
+    } else {
+      cl[m] = cd[m] = cu[m] = us[m] = zero;
+    }
+  }
+  const R h = R(t.h);
+  const R h2 = R(0.5) * h;
+  const R h6 = h / R(6);
+  int buf = 0;
+  // y = A x + f for the owned points; x is written to the shared buffer first.
+  auto stage = [&](const cpx<R>* x, const cpx<R>* f, cpx<R>* y) {
+    cpx<R>* s = sx + buf * ld;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m)
+      if (ok[m]) s[1 + threadIdx.x + m * blockDim.x] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      const int i = threadIdx.x + m * blockDim.x;
+      cpx<R> a = f[m];
+      if (ok[m]) {
+        cfma(a, cl[m], s[i]);
+        cfma(a, cd[m], x[m]);
+        cfma(a, cu[m], s[i + 2]);
+      }
+      y[m] = a;
+    }
+    buf ^= 1;
+  };
+  cpx<R> f0[PPT], fh[PPT], f1[PPT];
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) f0[m] = fh[m] = f1[m] = zero;
+  if (F != nullptr && t.n0 < t.n_forced) {
+#pragma unroll
+    for (int m = 0; m < PPT; ++m)
+      if (ok[m]) f0[m] = F[rbase + threadIdx.x + m * blockDim.x];
+  }
+  for (int s = 0; s < t.steps; ++s) {
+    const int64_t n = t.n0 + s;
+    const bool forced = (F != nullptr) && (n < t.n_forced);
+    if (forced) {
+#pragma unroll
+      for (int m = 0; m < PPT; ++m) {
+        if (ok[m]) {
+          const int64_t r = rbase + threadIdx.x + m * blockDim.x;
+          fh[m] = F[(int64_t)(2 * s + 1) * rows + r];
+          f1[m] = F[(int64_t)(2 * s + 2) * rows + r];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < PPT; ++m) f0[m] = fh[m] = f1[m] = zero;
+    }
+    if (Y != nullptr && s >= t.y_first) {
+#pragma unroll
+      for (int m = 0; m < PPT; ++m)
+        if (ok[m]) Y[(int64_t)s * rows + rbase + threadIdx.x + m * blockDim.x] = us[m];
+    }
+    cpx<R> k1[PPT], k2[PPT], k3[PPT], k4[PPT], x[PPT];
+    stage(us, f0, k1);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) x[m] = us[m] + h2 * k1[m];
+    stage(x, fh, k2);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) x[m] = us[m] + h2 * k2[m];
+    stage(x, fh, k3);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) x[m] = us[m] + h * k3[m];
+    stage(x, f1, k4);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      const cpx<R> sum = k1[m] + R(2) * k2[m] + R(2) * k3[m] + k4[m];
+      us[m] = us[m] + h6 * sum;
+      f0[m] = f1[m];
+    }
+  }
+  double nrm = 0.0;
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) {
+    if (ok[m]) {
+      u[rbase + threadIdx.x + m * blockDim.x] = us[m];
+      nrm += (double)us[m].re * (double)us[m].re + (double)us[m].im * (double)us[m].im;
+    }
+  }
+  // block reduction of |u|^2 for the norm monitor
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    if (norms != nullptr) norms[(int64_t)v * t.n_inst + inst] = tot;
+    if (!(tot < 1e300)) atomicExch(flag, 1);  // NaN or overflow
+  }
+}
+
+template <typename R>
+__global__ void gl1d_apply_kernel(Gl1dTile t, const cpx<R>* __restrict__ x, cpx<R>* __restrict__ y,
+                                  const int32_t* __restrict__ inst_of_point) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (p >= t.n) return;
+  const int inst = inst_of_point[p];
+  const int64_t a = t.inst_off[inst], b = t.inst_off[inst + 1];
+  const cpx<R>* lo = reinterpret_cast<const cpx<R>*>(t.lo);
+  const cpx<R>* di = reinterpret_cast<const cpx<R>*>(t.di);
+  const cpx<R>* up = reinterpret_cast<const cpx<R>*>(t.up);
+  const cpx<R>* xv = x + (int64_t)v * t.n;
+  cpx<R> acc = mk<R>(0, 0);
+  if (p > a) cfma(acc, lo[p], xv[p - 1]);
+  cfma(acc, di[p], xv[p]);
+  if (p + 1 < b) cfma(acc, up[p], xv[p + 1]);
+  y[(int64_t)v * t.n + p] = acc;
+}
+
+template <typename R, int PPT>
+cudaError_t launch_ppt(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms, int* flag,
+                       cudaStream_t st) {
+  int threads = (t.max_n + PPT - 1) / PPT;
+  threads = ((threads + 31) / 32) * 32;
+  const size_t smem = sizeof(cpx<R>) * 2 * (size_t)(t.max_n + 2);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(gl1d_tile_kernel<R, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)t.n_inst, (unsigned)t.kg);
+  gl1d_tile_kernel<R, PPT><<<grid, threads, smem, st>>>(t, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y, norms, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms, int* flag,
+                             cudaStream_t st) {
+  if (t.max_n <= 1024) return launch_ppt<R, 1>(t, u, F, Y, norms, flag, st);
+  if (t.max_n <= 2048) return launch_ppt<R, 2>(t, u, F, Y, norms, flag, st);
+  if (t.max_n <= 4096) return launch_ppt<R, 4>(t, u, F, Y, norms, flag, st);
+  return cudaErrorInvalidValue;
+}
+
+template <typename R>
+cudaError_t launch_gl1d_apply(const Gl1dTile& t, const int32_t* inst_of_point, const void* x, void* y,
+                              cudaStream_t st) {
+  dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)t.kg);
+  gl1d_apply_kernel<R><<<grid, 256, 0, st>>>(t, (const cpx<R>*)x, (cpx<R>*)y, inst_of_point);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gl1d_tile<double>(const Gl1dTile&, void*, const void*, void*, double*, int*,
+                                             cudaStream_t);
+template cudaError_t launch_gl1d_tile<float>(const Gl1dTile&, void*, const void*, void*, double*, int*,
+                                            cudaStream_t);
+template cudaError_t launch_gl1d_apply<double>(const Gl1dTile&, const int32_t*, const void*, void*, cudaStream_t);
+template cudaError_t launch_gl1d_apply<float>(const Gl1dTile&, const int32_t*, const void*, void*, cudaStream_t);
+
+}  // namespace rsv

@@ -1,0 +1,151 @@
+// Operator kinds: construction of the device coefficient arrays and the
+// dispatch of one march tile / one operator application to each kind's
+// kernels.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "rsv_ops.h"
+
+namespace rsv {
+
+namespace {
+
+template <typename R>
+std::vector<cpx<R>> narrow(const std::vector<std::complex<double>>& v) {
+  std::vector<cpx<R>> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = mk<R>((R)v[i].real(), (R)v[i].imag());
+  return o;
+}
+
+rsv_status upload_cvec(rsv_operator op, const std::vector<std::complex<double>>& v, void** dst) {
+  if (op->prec == RSV_PREC_FP64) {
+    auto o = narrow<double>(v);
+    return upload(op, o.data(), o.size() * sizeof(cpx<double>), dst);
+  }
+  auto o = narrow<float>(v);
+  return upload(op, o.data(), o.size() * sizeof(cpx<float>), dst);
+}
+
+}  // namespace
+
+// Linearised GL (Sec. 3, Eq. (GL_timeDomain) family) with central differences:
+//   (A u)_i = lo_i u_{i-1} + di_i u_i + up_i u_{i+1},
+//   lo = nu/(2dx) + gamma/dx^2, up = -nu/(2dx) + gamma/dx^2,
+//   di = -2 gamma/dx^2 + mu(x_i),  mu = mu0 + mu_shift + mu2 x^2,
+// Dirichlet zeros beyond each instance.  The adjoint (A^H) coefficients are
+//   lo^H_i = conj(up_{i-1}), di^H_i = conj(di_i), up^H_i = conj(lo_{i+1}).
+rsv_status build_gl1d(rsv_operator op, const rsv_operator_desc* d) {
+  if (d->n_instances < 1 || !d->gl_n || !d->gl_mu0) return fail(RSV_ERR_INVALID_ARG, "GL1D needs instances");
+  if (!(d->x1 > d->x0)) return fail(RSV_ERR_INVALID_ARG, "GL1D needs x1 > x0");
+  op->n_inst = d->n_instances;
+  int64_t tot = 0;
+  int maxn = 0;
+  for (int i = 0; i < d->n_instances; ++i) {
+    if (d->gl_n[i] < 2 || d->gl_n[i] > 4096) return fail(RSV_ERR_INVALID_ARG, "GL1D instance size must be 2..4096");
+    op->inst_off.push_back(tot);
+    op->inst_len.push_back(d->gl_n[i]);
+    tot += d->gl_n[i];
+    maxn = std::max(maxn, (int)d->gl_n[i]);
+  }
+  op->n = tot;
+  op->gl_max_n = maxn;
+  op->real_state = false;
+  const std::complex<double> nu(d->nu_re, d->nu_im), ga(d->gamma_re, d->gamma_im);
+  std::vector<std::complex<double>> lo(tot), di(tot), up(tot), alo(tot), adi(tot), aup(tot);
+  for (int i = 0; i < d->n_instances; ++i) {
+    const int64_t off = op->inst_off[i];
+    const int n = d->gl_n[i];
+    const double dx = (d->x1 - d->x0) / (double)(n + 1);
+    for (int p = 0; p < n; ++p) {
+      const double x = d->x0 + (p + 1) * dx;
+      const double mu = d->gl_mu0[i] + d->mu_shift + d->mu2 * x * x;
+      lo[off + p] = (p > 0) ? nu / (2.0 * dx) + ga / (dx * dx) : 0.0;
+      up[off + p] = (p < n - 1) ? -nu / (2.0 * dx) + ga / (dx * dx) : 0.0;
+      di[off + p] = -2.0 * ga / (dx * dx) + mu;
+    }
+    for (int p = 0; p < n; ++p) {
+      alo[off + p] = (p > 0) ? std::conj(up[off + p - 1]) : 0.0;
+      adi[off + p] = std::conj(di[off + p]);
+      aup[off + p] = (p < n - 1) ? std::conj(lo[off + p + 1]) : 0.0;
+    }
+  }
+  const std::vector<std::complex<double>>* arrs[6] = {&lo, &di, &up, &alo, &adi, &aup};
+  for (int a = 0; a < 6; ++a) {
+    rsv_status s = upload_cvec(op, *arrs[a], &op->tri[a]);
+    if (s != RSV_OK) return s;
+  }
+  return RSV_OK;
+}
+
+rsv_status build_dense(rsv_operator op, const rsv_operator_desc* d) {
+  return fail(RSV_ERR_INVALID_ARG, "dense operator kind is not built in this library version");
+}
+rsv_status build_adr2d(rsv_operator op, const rsv_operator_desc* d) {
+  return fail(RSV_ERR_INVALID_ARG, "ADR2D operator kind is not built in this library version");
+}
+rsv_status build_adv3d(rsv_operator op, const rsv_operator_desc* d) {
+  return fail(RSV_ERR_INVALID_ARG, "ADV3D operator kind is not built in this library version");
+}
+
+int default_tile_steps(rsv_operator op) { return 256; }
+
+int march_group_size(rsv_operator op, int k, int S) { return k; }
+
+size_t stage_scratch_bytes(rsv_operator op, int kg) { return 0; }
+
+static Gl1dTile gl1d_geom(rsv_operator op, bool adjoint, int kg) {
+  Gl1dTile g;
+  const int b = adjoint ? 3 : 0;
+  g.lo = op->tri[b];
+  g.di = op->tri[b + 1];
+  g.up = op->tri[b + 2];
+  g.inst_off = (const int64_t*)op->d_inst_off;
+  g.n_inst = op->n_inst;
+  g.max_n = op->gl_max_n;
+  g.n = op->n;
+  g.kg = kg;
+  g.h = op->h;
+  g.n0 = 0;
+  g.steps = 0;
+  g.n_forced = 0;
+  g.y_first = 0;
+  g.real_state = false;
+  return g;
+}
+
+template <typename R>
+cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const void* F, void* Y, double* norms) {
+  switch (op->kind) {
+    case RSV_OP_GL1D: {
+      Gl1dTile g = gl1d_geom(op, t.adjoint, t.kg);
+      g.n0 = t.n0;
+      g.steps = t.steps;
+      g.n_forced = t.n_forced;
+      g.y_first = t.y_first;
+      return launch_gl1d_tile<R>(g, state, F, Y, norms, op->d_flag, op->stream);
+    }
+    default:
+      return cudaErrorNotSupported;
+  }
+}
+
+template <typename R>
+cudaError_t apply_op(rsv_operator op, const void* x, int k, bool adjoint, void* y) {
+  switch (op->kind) {
+    case RSV_OP_GL1D: {
+      Gl1dTile g = gl1d_geom(op, adjoint, k);
+      return launch_gl1d_apply<R>(g, (const int32_t*)op->d_inst_of_point, x, y, op->stream);
+    }
+    default:
+      return cudaErrorNotSupported;
+  }
+}
+
+template cudaError_t march_tile<double>(rsv_operator, const MarchTile&, void*, const void*, void*, double*);
+template cudaError_t march_tile<float>(rsv_operator, const MarchTile&, void*, const void*, void*, double*);
+template cudaError_t apply_op<double>(rsv_operator, const void*, int, bool, void*);
+template cudaError_t apply_op<float>(rsv_operator, const void*, int, bool, void*);
+
+}  // namespace rsv

@@ -1,0 +1,459 @@
+// C ABI of librsv: operator objects, the frequency grid and twiddle table,
+// and the tile-by-tile driver of the direct and adjoint marches.
+//
+// Method (Sec. 2 of the paper): the action of the resolvent on Fourier
+// coefficients for all frequencies at once, by marching the linear system
+// with a forcing synthesised from the coefficients and Fourier-analysing the
+// response.  The march is cut into time tiles of S steps; per tile the
+// driver launches
+//   synthesis  F[0..2S] = forcing at the tile's step starts and midpoints
+//              (only while the forcing is on),
+//   march      S RK4 steps of the operator's fused stage kernel, storing the
+//              state of analysed steps in Y,
+//   analysis   acc[j] += sum_s Y[s] exp(-i w_j t_s) (only in the analysis window).
+// Schedules: SSRM (Sec. 2.3) forces n_trans + 1 windows of N_T steps and
+// analyses the last; TRM (Sec. 2.2) forces one window, then marches an
+// unforced tail, and analyses the whole record.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rsv_internal.h"
+#include "rsv_ops.h"
+
+namespace rsv {
+
+static thread_local std::string g_err;
+
+rsv_status fail(rsv_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+rsv_status cuda_fail(cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(e == cudaErrorMemoryAllocation ? RSV_ERR_OOM : RSV_ERR_CUDA, m);
+}
+
+rsv_status ensure(Workspace& w, size_t bytes) {
+  if (w.bytes >= bytes && w.ptr != nullptr) return RSV_OK;
+  if (w.ptr) cudaFree(w.ptr);
+  w.ptr = nullptr;
+  w.bytes = 0;
+  cudaError_t e = cudaMalloc(&w.ptr, bytes < 256 ? 256 : bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    w.ptr = nullptr;
+    return cuda_fail(e, "workspace allocation");
+  }
+  w.bytes = bytes;
+  return RSV_OK;
+}
+
+rsv_status upload(rsv_operator op, const void* host, size_t bytes, void** dst) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "operator allocation");
+  op->dev.push_back(p);
+  e = cudaMemcpy(p, host, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "operator upload");
+  *dst = p;
+  return RSV_OK;
+}
+
+static void prof_flush(rsv_operator op) {
+  Profiler& p = op->prof;
+  if (p.used == 0) return;
+  cudaStreamSynchronize(op->stream);
+  for (size_t i = 0; i < p.used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p.pool[2 * i], p.pool[2 * i + 1]) == cudaSuccess) {
+      p.ms[p.cat[i]] += t;
+      p.launches[p.cat[i]] += 1;
+    }
+  }
+  p.used = 0;
+}
+
+ProfScope::ProfScope(rsv_operator o, int c) : op(o), cat(c) {
+  Profiler& p = op->prof;
+  if (!p.on) return;
+  if (p.used >= 4096) prof_flush(op);
+  if (2 * p.used + 2 > p.pool.size()) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      p.pool.push_back(e);
+    }
+    p.cat.push_back(0);
+  }
+  p.cat[p.used] = c;
+  cudaEventRecord(p.pool[2 * p.used], op->stream);
+}
+
+ProfScope::~ProfScope() {
+  Profiler& p = op->prof;
+  if (!p.on) return;
+  cudaEventRecord(p.pool[2 * p.used + 1], op->stream);
+  p.used += 1;
+}
+
+size_t elem_bytes(rsv_operator op) { return op->prec == RSV_PREC_FP64 ? 8 : 4; }
+size_t coef_bytes(rsv_operator op) { return 2 * elem_bytes(op); }
+size_t state_elem_bytes(rsv_operator op) { return op->real_state ? elem_bytes(op) : coef_bytes(op); }
+
+}  // namespace rsv
+
+using namespace rsv;
+
+rsv_operator_s::~rsv_operator_s() {
+  for (void* p : dev) cudaFree(p);
+  Workspace* ws[] = {&ws_state, &ws_ftile, &ws_ysnap, &ws_acc, &ws_norm, &ws_glue_a, &ws_glue_b, &ws_gram, &ws_small};
+  for (Workspace* w : ws)
+    if (w->ptr) cudaFree(w->ptr);
+  if (d_tw) cudaFree(d_tw);
+  if (d_pj) cudaFree(d_pj);
+  if (d_cw) cudaFree(d_cw);
+  if (d_flag) cudaFree(d_flag);
+  for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
+}
+
+extern "C" rsv_status rsv_profile_enable(rsv_operator op, int32_t enable) {
+  if (!op) return fail(RSV_ERR_INVALID_ARG, "null operator");
+  if (!enable) prof_flush(op);
+  op->prof.on = enable != 0;
+  return RSV_OK;
+}
+
+extern "C" rsv_status rsv_profile_reset(rsv_operator op) {
+  if (!op) return fail(RSV_ERR_INVALID_ARG, "null operator");
+  prof_flush(op);
+  for (int c = 0; c < 4; ++c) {
+    op->prof.launches[c] = 0;
+    op->prof.ms[c] = 0.0;
+  }
+  return RSV_OK;
+}
+
+extern "C" rsv_status rsv_profile_read(rsv_operator op, int32_t category, int64_t* launches, double* ms) {
+  if (!op || category < 0 || category > 3) return fail(RSV_ERR_INVALID_ARG, "bad profile query");
+  prof_flush(op);
+  if (launches) *launches = op->prof.launches[category];
+  if (ms) *ms = op->prof.ms[category];
+  return RSV_OK;
+}
+
+extern "C" const char* rsv_last_error(void) { return g_err.c_str(); }
+extern "C" const char* rsv_version(void) { return "rsv 0.1 (sm_103a)"; }
+
+extern "C" rsv_status rsv_create_operator(const rsv_operator_desc* d, void* stream, rsv_operator* out) {
+  if (!d || !out) return fail(RSV_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (d->precision != RSV_PREC_FP64 && d->precision != RSV_PREC_FP32)
+    return fail(RSV_ERR_INVALID_ARG, "unknown precision");
+  if (!(d->dt > 0.0)) return fail(RSV_ERR_INVALID_ARG, "dt must be positive");
+  rsv_operator op = new rsv_operator_s();
+  op->kind = d->kind;
+  op->prec = d->precision;
+  op->dt = d->dt;
+  op->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&op->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  rsv_status s;
+  switch (d->kind) {
+    case RSV_OP_GL1D: s = build_gl1d(op, d); break;
+    case RSV_OP_DENSE: s = build_dense(op, d); break;
+    case RSV_OP_ADR2D: s = build_adr2d(op, d); break;
+    case RSV_OP_ADV3D: s = build_adv3d(op, d); break;
+    default: s = fail(RSV_ERR_INVALID_ARG, "unknown operator kind");
+  }
+  if (s == RSV_OK) {
+    // instance tables shared by every kind
+    std::vector<int64_t> off(op->n_inst + 1);
+    std::vector<int32_t> iop(op->n);
+    for (int i = 0; i < op->n_inst; ++i) {
+      off[i] = op->inst_off[i];
+      for (int64_t p = op->inst_off[i]; p < op->inst_off[i] + op->inst_len[i]; ++p) iop[p] = i;
+    }
+    off[op->n_inst] = op->n;
+    s = upload(op, off.data(), off.size() * sizeof(int64_t), &op->d_inst_off);
+    if (s == RSV_OK) s = upload(op, iop.data(), iop.size() * sizeof(int32_t), &op->d_inst_of_point);
+    if (s == RSV_OK) {
+      cudaError_t e = cudaMalloc(&op->d_flag, sizeof(int));
+      if (e != cudaSuccess) s = cuda_fail(e, "flag allocation");
+    }
+  }
+  if (s != RSV_OK) {
+    delete op;
+    return s;
+  }
+  *out = op;
+  return RSV_OK;
+}
+
+extern "C" void rsv_destroy_operator(rsv_operator op) {
+  if (!op) return;
+  cudaStreamSynchronize(op->stream);
+  delete op;
+}
+
+extern "C" rsv_status rsv_operator_info(rsv_operator op, int64_t* n, int32_t* n_instances, int32_t* real_state) {
+  if (!op) return fail(RSV_ERR_INVALID_ARG, "null operator");
+  if (n) *n = op->n;
+  if (n_instances) *n_instances = op->n_inst;
+  if (real_state) *real_state = op->real_state ? 1 : 0;
+  return RSV_OK;
+}
+
+extern "C" rsv_status rsv_instance_range(rsv_operator op, int32_t i, int64_t* offset, int64_t* length) {
+  if (!op || i < 0 || i >= op->n_inst) return fail(RSV_ERR_INVALID_ARG, "bad instance index");
+  if (offset) *offset = op->inst_off[i];
+  if (length) *length = op->inst_len[i];
+  return RSV_OK;
+}
+
+// Frequencies: w_j = (m_j + phi) dw with integer m_j and common phi in {0, 1/2}
+// (Sec. 2.3, Delta omega = 2 pi / T).  The twiddle table holds exp(i pi q / (2 N_T))
+// for q < 4 N_T, so exp(i w_j (2n + sigma) h / 2) = table[p_j (2n + sigma) mod 4 N_T]
+// with p_j = 2 (m_j + phi), exact in the integer index for any t.
+extern "C" rsv_status rsv_set_frequencies(rsv_operator op, const double* omega, int32_t n_omega, double dw,
+                                          int64_t* n_steps_per_window, double* h_out) {
+  if (!op || !omega || n_omega < 1) return fail(RSV_ERR_INVALID_ARG, "bad frequency arguments");
+  if (dw <= 0.0) {
+    if (n_omega < 2) return fail(RSV_ERR_INVALID_ARG, "a single frequency needs an explicit dw");
+    std::vector<double> srt(omega, omega + n_omega);
+    std::sort(srt.begin(), srt.end());
+    dw = 0.0;
+    for (int i = 1; i < n_omega; ++i) {
+      const double g = srt[i] - srt[i - 1];
+      if (g <= 0.0) return fail(RSV_ERR_INVALID_ARG, "repeated frequency");
+      if (dw == 0.0 || g < dw) dw = g;
+    }
+  }
+  const double r0 = omega[0] / dw;
+  const double frac = r0 - std::floor(r0);
+  const double phi = std::fabs(frac - 0.5) < 1e-6 ? 0.5 : 0.0;
+  std::vector<int64_t> pj(n_omega);
+  for (int j = 0; j < n_omega; ++j) {
+    const double r = omega[j] / dw - phi;
+    const double m = std::nearbyint(r);
+    if (std::fabs(r - m) > 1e-6)
+      return fail(RSV_ERR_NOT_COMMENSURATE, "frequency " + std::to_string(j) + " is not on the grid (m + phi) dw");
+    pj[j] = (int64_t)(2.0 * m + 2.0 * phi);
+  }
+  const double period = 2.0 * M_PI / dw;
+  const int64_t n_t = (int64_t)std::ceil(period / op->dt - 1e-9);
+  if (n_t < 1 || n_t > (int64_t)1 << 40) return fail(RSV_ERR_INVALID_ARG, "window length out of range");
+  for (int j = 0; j < n_omega; ++j) {
+    for (int l = 0; l < j; ++l) {
+      const int64_t dm = (pj[j] - pj[l]) / 2;
+      if (dm % n_t == 0) return fail(RSV_ERR_NOT_COMMENSURATE, "two frequencies alias on the window");
+    }
+  }
+  const int64_t m4 = 4 * n_t;
+  std::vector<cpx<double>> tab(m4);
+  for (int64_t q = 0; q < m4; ++q) {
+    // reduce to the first octant by symmetry so that every entry is correctly rounded
+    const int64_t quad = q / n_t, rr = q % n_t;  // angle = (quad + rr / n_t) * pi/2
+    double c, s;
+    if (2 * rr <= n_t) {
+      const double a = M_PI_2 * (double)rr / (double)n_t;
+      c = std::cos(a);
+      s = std::sin(a);
+    } else {
+      const double a = M_PI_2 * (double)(n_t - rr) / (double)n_t;
+      c = std::sin(a);
+      s = std::cos(a);
+    }
+    double re, im;
+    switch (quad) {
+      case 0: re = c; im = s; break;
+      case 1: re = -s; im = c; break;
+      case 2: re = -c; im = -s; break;
+      default: re = s; im = -c; break;
+    }
+    tab[q] = mk<double>(re, im);
+  }
+  if (op->d_tw) cudaFree(op->d_tw);
+  if (op->d_pj) cudaFree(op->d_pj);
+  if (op->d_cw) cudaFree(op->d_cw);
+  op->d_tw = nullptr;
+  op->d_pj = nullptr;
+  op->d_cw = nullptr;
+  cudaError_t e;
+  if (op->prec == RSV_PREC_FP64) {
+    e = cudaMalloc(&op->d_tw, m4 * sizeof(cpx<double>));
+    if (e == cudaSuccess) e = cudaMemcpy(op->d_tw, tab.data(), m4 * sizeof(cpx<double>), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<cpx<float>> t32(m4);
+    for (int64_t q = 0; q < m4; ++q) t32[q] = mk<float>((float)tab[q].re, (float)tab[q].im);
+    e = cudaMalloc(&op->d_tw, m4 * sizeof(cpx<float>));
+    if (e == cudaSuccess) e = cudaMemcpy(op->d_tw, t32.data(), m4 * sizeof(cpx<float>), cudaMemcpyHostToDevice);
+  }
+  std::vector<float> cw(n_omega);
+  for (int j = 0; j < n_omega; ++j) cw[j] = (pj[j] == 0) ? 1.0f : 2.0f;
+  if (e == cudaSuccess) e = cudaMalloc(&op->d_pj, n_omega * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMemcpy(op->d_pj, pj.data(), n_omega * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&op->d_cw, n_omega * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(op->d_cw, cw.data(), n_omega * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "twiddle table");
+  op->omega.assign(omega, omega + n_omega);
+  op->pj = pj;
+  op->n_omega = n_omega;
+  op->dw = dw;
+  op->phi = phi;
+  op->period = period;
+  op->n_t = n_t;
+  op->h = period / (double)n_t;
+  op->have_freq = true;
+  if (n_steps_per_window) *n_steps_per_window = n_t;
+  if (h_out) *h_out = op->h;
+  return RSV_OK;
+}
+
+namespace rsv {
+
+struct Schedule {
+  int64_t total, first, forced;
+};
+
+static rsv_status make_schedule(rsv_operator op, const rsv_march_opts* o, Schedule* s) {
+  rsv_march_opts def{};
+  if (!o) o = &def;
+  if (o->variant == RSV_SSRM) {
+    if (o->n_transient_windows < 0) return fail(RSV_ERR_INVALID_ARG, "n_transient_windows < 0");
+    s->total = (int64_t)(o->n_transient_windows + 1) * op->n_t;
+    s->first = (int64_t)o->n_transient_windows * op->n_t;
+    s->forced = s->total;
+  } else if (o->variant == RSV_TRM) {
+    if (o->tail_steps < 0) return fail(RSV_ERR_INVALID_ARG, "tail_steps < 0");
+    s->total = op->n_t + o->tail_steps;
+    s->first = 0;
+    s->forced = op->n_t;
+  } else {
+    return fail(RSV_ERR_INVALID_ARG, "unknown variant");
+  }
+  return RSV_OK;
+}
+
+template <typename R>
+static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out,
+                             bool adjoint) {
+  Schedule sc;
+  rsv_status st = make_schedule(op, opts, &sc);
+  if (st != RSV_OK) return st;
+  const int S = (opts && opts->tile_steps > 0) ? opts->tile_steps : default_tile_steps(op);
+  const int kg = march_group_size(op, k, S);
+  const int64_t n = op->n;
+  const size_t se = state_elem_bytes(op);
+  const cudaStream_t stream = op->stream;
+  cudaError_t e;
+  const int64_t rows_max = (int64_t)kg * n;
+  if ((st = ensure(op->ws_state, rows_max * se + stage_scratch_bytes(op, kg))) != RSV_OK) return st;
+  if ((st = ensure(op->ws_ftile, (size_t)(2 * S + 1) * rows_max * se)) != RSV_OK) return st;
+  if ((st = ensure(op->ws_ysnap, (size_t)S * rows_max * se)) != RSV_OK) return st;
+  if ((st = ensure(op->ws_norm, (size_t)kg * op->n_inst * sizeof(double))) != RSV_OK) return st;
+  const bool acc_in_out = (op->prec == RSV_PREC_FP64);
+  if (!acc_in_out && (st = ensure(op->ws_acc, (size_t)op->n_omega * rows_max * sizeof(cpx<double>))) != RSV_OK)
+    return st;
+  if ((e = cudaMemsetAsync(op->d_flag, 0, sizeof(int), stream)) != cudaSuccess) return cuda_fail(e, "flag reset");
+  const size_t ce = coef_bytes(op);
+  for (int v0 = 0; v0 < k; v0 += kg) {
+    const int kv = std::min(kg, k - v0);
+    const int64_t rows = (int64_t)kv * n;
+    cpx<double>* acc;
+    int64_t acc_stride;
+    if (acc_in_out) {
+      acc = reinterpret_cast<cpx<double>*>(out) + (int64_t)v0 * n;
+      acc_stride = (int64_t)k * n;
+      e = cudaMemset2DAsync(acc, acc_stride * sizeof(cpx<double>), 0, rows * sizeof(cpx<double>), op->n_omega,
+                            stream);
+    } else {
+      acc = reinterpret_cast<cpx<double>*>(op->ws_acc.ptr);
+      acc_stride = rows;
+      e = cudaMemsetAsync(acc, 0, (size_t)op->n_omega * rows * sizeof(cpx<double>), stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(op->ws_state.ptr, 0, rows * se, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "march reset");
+    TileGeom g;
+    g.rows = rows;
+    g.coef_stride = (int64_t)k * n;
+    g.n_omega = op->n_omega;
+    g.sgn = adjoint ? -1 : 1;
+    g.m4 = 4 * op->n_t;
+    const void* fh = static_cast<const char*>(in) + (size_t)v0 * n * ce;
+    for (int64_t n0 = 0; n0 < sc.total; n0 += S) {
+      g.n0 = n0;
+      g.steps = (int)std::min<int64_t>(S, sc.total - n0);
+      const bool forced = n0 < sc.forced;
+      const bool analysed = n0 + g.steps > sc.first;
+      if (forced) {
+        ProfScope ps(op, PROF_SYNTH);
+        e = launch_synth<R>(g, fh, op->d_tw, op->d_pj, op->d_cw, op->real_state, op->ws_ftile.ptr, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "synthesis");
+      }
+      const int y_first = analysed ? (int)std::max<int64_t>(0, sc.first - n0) : g.steps;
+      MarchTile mt;
+      mt.n0 = n0;
+      mt.steps = g.steps;
+      mt.n_forced = sc.forced;
+      mt.y_first = y_first;
+      mt.kg = kv;
+      mt.adjoint = adjoint;
+      {
+        ProfScope ps(op, PROF_MARCH);
+        e = march_tile<R>(op, mt, op->ws_state.ptr, forced ? op->ws_ftile.ptr : nullptr,
+                          analysed ? op->ws_ysnap.ptr : nullptr, (double*)op->ws_norm.ptr);
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "march tile");
+      if (analysed) {
+        ProfScope ps(op, PROF_ANALYSIS);
+        e = launch_analysis<R>(g, op->ws_ysnap.ptr, y_first, g.steps, op->d_tw, op->d_pj, op->real_state, acc,
+                               acc_stride, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "analysis");
+      }
+    }
+    void* o = static_cast<char*>(out) + (size_t)v0 * n * ce;
+    e = launch_finish<R>(acc, acc_stride, op->n_omega, rows, 1.0 / (double)op->n_t, o, (int64_t)k * n, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "finish");
+  }
+  int flag = 0;
+  e = cudaMemcpyAsync(&flag, op->d_flag, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "march");
+  if (flag) return fail(RSV_ERR_DIVERGED, "state norm became non-finite during the march");
+  return RSV_OK;
+}
+
+rsv_status march_any(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out, bool adjoint) {
+  if (!op || !in || !out || k < 1) return fail(RSV_ERR_INVALID_ARG, "bad march arguments");
+  if (!op->have_freq) return fail(RSV_ERR_STATE, "rsv_set_frequencies must come first");
+  if (in == out) return fail(RSV_ERR_INVALID_ARG, "input and output blocks must not alias");
+  return op->prec == RSV_PREC_FP64 ? march_impl<double>(op, in, k, opts, out, adjoint)
+                                   : march_impl<float>(op, in, k, opts, out, adjoint);
+}
+
+}  // namespace rsv
+
+extern "C" rsv_status rsv_march_direct(rsv_operator op, const void* f_hat, int32_t k, const rsv_march_opts* opts,
+                                       void* y_hat) {
+  return march_any(op, f_hat, k, opts, y_hat, false);
+}
+
+extern "C" rsv_status rsv_march_adjoint(rsv_operator op, const void* y_hat, int32_t k, const rsv_march_opts* opts,
+                                        void* w_hat) {
+  return march_any(op, y_hat, k, opts, w_hat, true);
+}
+
+extern "C" rsv_status rsv_apply_operator(rsv_operator op, const void* x, int32_t k, int32_t adjoint, void* y) {
+  if (!op || !x || !y || k < 1) return fail(RSV_ERR_INVALID_ARG, "bad apply arguments");
+  cudaError_t e = op->prec == RSV_PREC_FP64 ? apply_op<double>(op, x, k, adjoint != 0, y)
+                                            : apply_op<float>(op, x, k, adjoint != 0, y);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(op->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "apply");
+  return RSV_OK;
+}

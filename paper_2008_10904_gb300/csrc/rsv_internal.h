@@ -1,0 +1,210 @@
+// Internal declarations of librsv: complex helpers, the operator object,
+// and the kernel launchers each .cu file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rsv.h"
+
+namespace rsv {
+
+// ---------------------------------------------------------------------------
+// Complex numbers stored (re, im) interleaved, as at the ABI.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct alignas(2 * sizeof(R)) cpx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> mk(R a, R b) {
+  cpx<R> c;
+  c.re = a;
+  c.im = b;
+  return c;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.re + b.re, a.im + b.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.re - b.re, a.im - b.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) {
+  return mk<R>(s * a.re, s * a.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> conjg(cpx<R> a) {
+  return mk<R>(a.re, -a.im);
+}
+// acc += a * b
+template <typename R>
+__host__ __device__ __forceinline__ void cfma(cpx<R>& acc, cpx<R> a, cpx<R> b) {
+  acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(a.im, b.re, acc.im));
+}
+// acc += conj(a) * b
+template <typename R>
+__host__ __device__ __forceinline__ void cfma_conj(cpx<R>& acc, cpx<R> a, cpx<R> b) {
+  acc.re = fma(a.re, b.re, fma(a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(-a.im, b.re, acc.im));
+}
+
+// Phase index of exp(i w_j t) at t = (2 n + sigma) h / 2: q = sgn p_j (2n + sigma) mod 4 N_T,
+// with p_j = 2 (m_j + phi) an integer; table[q] = exp(i pi q / (2 N_T)).
+__host__ __device__ __forceinline__ int64_t phase_index(int64_t pj, int64_t half_steps, int64_t m4) {
+  int64_t q = (pj * half_steps) % m4;
+  return q < 0 ? q + m4 : q;
+}
+
+// ---------------------------------------------------------------------------
+// Operator object
+// ---------------------------------------------------------------------------
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Per-category CUDA-event accounting of kernel launches (rsv_profile_*).
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> cat;  // category of each recorded pair (events 2i, 2i+1)
+  size_t used = 0;
+  int64_t launches[4] = {0, 0, 0, 0};
+  double ms[4] = {0, 0, 0, 0};
+};
+
+}  // namespace rsv
+
+struct rsv_operator_s {
+  int kind = 0;
+  int prec = 0;
+  bool real_state = false;
+  double dt = 0.0;
+  int64_t n = 0;                        // state length (all instances, all components)
+  int n_inst = 1;
+  std::vector<int64_t> inst_off, inst_len;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+
+  // frequencies
+  bool have_freq = false;
+  int n_omega = 0;
+  std::vector<double> omega;
+  std::vector<int64_t> pj;              // 2 (m_j + phi)
+  double dw = 0.0, phi = 0.0, period = 0.0, h = 0.0;
+  int64_t n_t = 0;
+  void* d_tw = nullptr;                 // twiddle table [4 N_T], cpx<double> or cpx<float>
+  int64_t* d_pj = nullptr;              // [n_omega]
+  float* d_cw = nullptr;                // real-state synthesis weights c_j (1 at w = 0, else 2)
+
+  // device arrays of the operator (kind specific)
+  std::vector<void*> dev;               // freed at destroy
+  void* d_inst_off = nullptr;           // int64 [n_inst + 1]
+  void* d_inst_of_point = nullptr;      // int32 [n]
+  // GL1D: tridiagonal coefficients, direct then adjoint: lo, di, up
+  void* tri[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int gl_max_n = 0;
+  // DENSE: A and A^H, row-major, element type of the precision
+  void* dense[2] = {nullptr, nullptr};
+  // stencil kinds: base-flow fields
+  void* fld[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double c_dx = 0, c_dy = 0, c_dz = 0;
+  int nx = 0, ny = 0, nz = 0;
+  double visc = 0;
+
+  // march workspace (grown on demand)
+  rsv::Workspace ws_state, ws_ftile, ws_ysnap, ws_acc, ws_norm, ws_glue_a, ws_glue_b, ws_gram, ws_small;
+  int* d_flag = nullptr;
+  rsv::Profiler prof;
+
+  ~rsv_operator_s();
+};
+
+namespace rsv {
+
+// Thread-local error message; returns the status for convenience.
+rsv_status fail(rsv_status s, const std::string& msg);
+rsv_status cuda_fail(cudaError_t e, const char* where);
+rsv_status ensure(Workspace& w, size_t bytes);
+
+// Brackets one kernel launch with profiling events when profiling is on.
+struct ProfScope {
+  rsv_operator op;
+  int cat;
+  ProfScope(rsv_operator o, int c);
+  ~ProfScope();
+};
+enum { PROF_SYNTH = 0, PROF_MARCH = 1, PROF_ANALYSIS = 2, PROF_GLUE = 3 };
+
+// ----- launchers (contract_kernels.cu) -------------------------------------
+struct TileGeom {
+  int64_t rows;        // rows in this vector group = kg * n
+  int64_t coef_stride; // stride between frequencies in the coefficient block
+  int n_omega;
+  int64_t n0;          // first step of the tile
+  int steps;           // steps in the tile
+  int sgn;             // +1 direct, -1 adjoint (frequencies negated)
+  int64_t m4;          // 4 N_T
+};
+
+// F[tau][r] = sum_j c_j x(table[q_j(2 n0 + tau)] * fhat[j][r]), tau = 0..2*steps
+template <typename R>
+cudaError_t launch_synth(const TileGeom& g, const void* fhat, const void* tw, const int64_t* pj,
+                         const float* cw, bool real_state, void* F, cudaStream_t st);
+// acc[j][r] += sum_{s in [s0, s1)} conj(table[q_j(2 (n0 + s))]) Y[s][r]
+template <typename R>
+cudaError_t launch_analysis(const TileGeom& g, const void* Y, int s0, int s1, const void* tw,
+                            const int64_t* pj, bool real_state, cpx<double>* acc, int64_t acc_stride,
+                            cudaStream_t st);
+// out[j][r] = acc[j][r] * scale (converted to the element type R)
+template <typename R>
+cudaError_t launch_finish(const cpx<double>* acc, int64_t acc_stride, int n_omega, int64_t rows,
+                          double scale, void* out, int64_t out_stride, cudaStream_t st);
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+// ----- GL1D (gl1d_kernels.cu) ---------------------------------------------
+struct Gl1dTile {
+  const void* lo;
+  const void* di;
+  const void* up;
+  const int64_t* inst_off;  // [n_inst + 1]
+  int n_inst, max_n;
+  int64_t n;                // points per vector
+  int kg;                   // vectors in the group
+  double h;
+  int64_t n0;
+  int steps;
+  int64_t n_forced;         // forcing active for steps < n_forced
+  int y_first;              // store the state of tile steps s >= y_first into Y
+  bool real_state;
+};
+template <typename R>
+cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms,
+                             int* flag, cudaStream_t st);
+template <typename R>
+cudaError_t launch_gl1d_apply(const Gl1dTile& t, const int32_t* inst_of_point, const void* x, void* y,
+                              cudaStream_t st);
+
+// ----- glue (glue_kernels.cu) ----------------------------------------------
+// G[j][i][a][b] = sum_{p in instance i} conj(X[j][a][p]) X[j][b][p]
+template <typename R>
+cudaError_t launch_gram(const void* X, int n_omega, int k, int64_t n, const int64_t* inst_off, int n_inst,
+                        cpx<double>* G, cudaStream_t st);
+// Out[j][b][p] = sum_a In[j][a][p] * M[j][inst(p)][a][b] * colscale[j][inst][b]
+template <typename R>
+cudaError_t launch_combine(const void* In, int n_omega, int ka, int kb, int64_t n, const int32_t* inst_of_point,
+                           int n_inst, const cpx<double>* M, void* Out, int64_t out_k, cudaStream_t st);
+
+}  // namespace rsv

@@ -1,0 +1,294 @@
+"""Python binding of librsv (ctypes), one function per C-ABI entry point, same names.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Buffers are torch CUDA tensors (their data_ptr() is passed) or raw
+integer device pointers; the operator's stream is torch's current stream at
+creation unless one is given.  If librsv.so is missing or cannot be loaded,
+`load()` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librsv.so")
+
+RSV_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "NOT_COMMENSURATE", 4: "DIVERGED", 5: "TIMEOUT",
+          6: "OOM", 7: "CUDA", 8: "STATE"}
+RSV_OP_GL1D, RSV_OP_DENSE, RSV_OP_ADR2D, RSV_OP_ADV3D = 0, 1, 2, 3
+RSV_PREC_FP64, RSV_PREC_FP32 = 0, 1
+RSV_SSRM, RSV_TRM = 0, 1
+
+
+class RsvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rsv_operator_desc(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("precision", ctypes.c_int32), ("dt", ctypes.c_double),
+        ("n_instances", ctypes.c_int32), ("gl_n", ctypes.POINTER(ctypes.c_int32)),
+        ("gl_mu0", ctypes.POINTER(ctypes.c_double)), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("nu_re", ctypes.c_double), ("nu_im", ctypes.c_double), ("gamma_re", ctypes.c_double),
+        ("gamma_im", ctypes.c_double), ("mu_shift", ctypes.c_double), ("mu2", ctypes.c_double),
+        ("dense_n", ctypes.c_int32), ("dense_a", ctypes.POINTER(ctypes.c_double)),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("visc", ctypes.c_double), ("kappa", ctypes.c_double), ("jet_delta", ctypes.c_double),
+        ("sponge_amp", ctypes.c_double), ("sponge_cells", ctypes.c_int32),
+        ("delta0", ctypes.c_double), ("delta1", ctypes.c_double),
+    ]
+
+
+class rsv_march_opts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("n_transient_windows", ctypes.c_int32),
+                ("tail_steps", ctypes.c_int64), ("tile_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_ENTRY_POINTS = {
+    "rsv_create_operator": (ctypes.c_int, [ctypes.POINTER(rsv_operator_desc), ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "rsv_destroy_operator": (None, [ctypes.c_void_p]),
+    "rsv_operator_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "rsv_instance_range": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "rsv_set_frequencies": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                           ctypes.c_double, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "rsv_march_direct": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
+    "rsv_march_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
+    "rsv_gains_modes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.POINTER(rsv_march_opts),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p]),
+    "rsv_apply_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_void_p]),
+    "rsv_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "rsv_profile_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "rsv_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "rsv_last_error": (ctypes.c_char_p, []),
+    "rsv_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load librsv.so (built by paper_2008_10904_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librsv.so not built at {path}: run paper_2008_10904_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _ENTRY_POINTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_ENTRY_POINTS)
+
+
+def _check(status: int):
+    if status != RSV_OK:
+        raise RsvError(status, _lib.rsv_last_error().decode())
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous CUDA tensors")
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def _opts(variant="ssrm", n_transient_windows=0, tail_steps=0, tile_steps=0):
+    return rsv_march_opts(RSV_SSRM if variant == "ssrm" else RSV_TRM, int(n_transient_windows),
+                          int(tail_steps), int(tile_steps), 0)
+
+
+class Operator:
+    """Handle plus the host arrays its descriptor points to."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def __int__(self):
+        return self.handle.value
+
+
+def rsv_create_operator(desc: rsv_operator_desc, stream=None, keep=()) -> Operator:
+    load()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    h = ctypes.c_void_p()
+    _check(_lib.rsv_create_operator(ctypes.byref(desc), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return Operator(h, keep)
+
+
+def rsv_destroy_operator(op: Operator):
+    if op is not None and op.handle:
+        _lib.rsv_destroy_operator(op.handle)
+        op.handle = ctypes.c_void_p()
+
+
+def rsv_operator_info(op: Operator):
+    n, ni, rs = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.rsv_operator_info(op.handle, ctypes.byref(n), ctypes.byref(ni), ctypes.byref(rs)))
+    return n.value, ni.value, bool(rs.value)
+
+
+def rsv_instance_range(op: Operator, i: int):
+    o, l = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.rsv_instance_range(op.handle, i, ctypes.byref(o), ctypes.byref(l)))
+    return o.value, l.value
+
+
+def rsv_set_frequencies(op: Operator, omegas, dw: float = 0.0):
+    om = np.ascontiguousarray(np.asarray(omegas, dtype=np.float64))
+    nt, h = ctypes.c_int64(), ctypes.c_double()
+    _check(_lib.rsv_set_frequencies(op.handle, om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(om),
+                                    float(dw), ctypes.byref(nt), ctypes.byref(h)))
+    return nt.value, h.value
+
+
+def rsv_march_direct(op: Operator, f_hat, k: int, y_hat, **opts):
+    o = _opts(**opts)
+    _check(_lib.rsv_march_direct(op.handle, _ptr(f_hat), int(k), ctypes.byref(o), _ptr(y_hat)))
+
+
+def rsv_march_adjoint(op: Operator, y_hat, k: int, w_hat, **opts):
+    o = _opts(**opts)
+    _check(_lib.rsv_march_adjoint(op.handle, _ptr(y_hat), int(k), ctypes.byref(o), _ptr(w_hat)))
+
+
+def rsv_gains_modes(op: Operator, omega_block, k: int, n_power_iter: int, n_modes: int, gains: np.ndarray,
+                    forcing_modes=None, response_modes=None, **opts):
+    """gains: host float64 array [n_instances][n_omega][n_modes], filled in place."""
+    if gains.dtype != np.float64 or not gains.flags.c_contiguous:
+        raise ValueError("gains must be a C-contiguous float64 array")
+    o = _opts(**opts)
+    _check(_lib.rsv_gains_modes(op.handle, _ptr(omega_block), int(k), int(n_power_iter), int(n_modes),
+                                ctypes.byref(o), gains.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                _ptr(forcing_modes), _ptr(response_modes)))
+    return gains
+
+
+def rsv_apply_operator(op: Operator, x, k: int, adjoint: bool, y):
+    _check(_lib.rsv_apply_operator(op.handle, _ptr(x), int(k), int(bool(adjoint)), _ptr(y)))
+
+
+PROFILE_CATEGORIES = ("synthesis", "march", "analysis", "glue")
+
+
+def rsv_profile_enable(op: Operator, enable: bool):
+    _check(_lib.rsv_profile_enable(op.handle, int(bool(enable))))
+
+
+def rsv_profile_reset(op: Operator):
+    _check(_lib.rsv_profile_reset(op.handle))
+
+
+def rsv_profile_read(op: Operator, category: int):
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    _check(_lib.rsv_profile_read(op.handle, int(category), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def rsv_last_error() -> str:
+    load()
+    return _lib.rsv_last_error().decode()
+
+
+def rsv_version() -> str:
+    load()
+    return _lib.rsv_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# Descriptor marshalling from the workload parameter objects
+# ---------------------------------------------------------------------------
+def desc_for(system, dt: float, precision: int):
+    """rsv_operator_desc for a workloads.GL1D / Dense / ADR2D / ADV3D object.
+
+    Returns (desc, keep) where `keep` holds the host arrays the descriptor
+    points to (they must stay alive until rsv_create_operator returns).
+    """
+    d = rsv_operator_desc()
+    d.precision = precision
+    d.dt = float(dt)
+    keep = []
+    name = type(system).__name__
+    if name == "GL1D":
+        d.kind = RSV_OP_GL1D
+        n = np.ascontiguousarray(np.asarray(system.n, dtype=np.int32))
+        mu0 = np.ascontiguousarray(np.asarray(system.mu0, dtype=np.float64))
+        keep += [n, mu0]
+        d.n_instances = len(n)
+        d.gl_n = n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.gl_mu0 = mu0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.x0, d.x1 = system.x0, system.x1
+        d.nu_re, d.nu_im = system.nu.real, system.nu.imag
+        d.gamma_re, d.gamma_im = system.gamma.real, system.gamma.imag
+        d.mu_shift, d.mu2 = system.mu_shift, system.mu2
+    elif name == "Dense":
+        raise ValueError("a dense system needs its matrix: use desc_dense")
+    elif name == "ADR2D":
+        d.kind = RSV_OP_ADR2D
+        d.nx, d.ny = system.nx, system.ny
+        d.lx, d.ly = system.lx, system.ly
+        d.visc, d.kappa, d.jet_delta = system.visc, system.kappa, system.jet_delta
+        d.sponge_cells, d.sponge_amp = system.sponge_cells, system.sponge_amp
+    elif name == "ADV3D":
+        d.kind = RSV_OP_ADV3D
+        d.nx, d.ny, d.nz = system.nx, system.ny, system.nz
+        d.lx, d.ly, d.lz = system.lx, system.ly, system.lz
+        d.visc, d.delta0, d.delta1 = system.visc, system.delta0, system.delta1
+    else:
+        raise ValueError(name)
+    return d, keep
+
+
+def desc_dense(a: np.ndarray, dt: float, precision: int):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    d = rsv_operator_desc()
+    d.kind = RSV_OP_DENSE
+    d.precision = precision
+    d.dt = float(dt)
+    d.dense_n = a.shape[0]
+    d.dense_a = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return d, [a]
+
+
+def create_for_workload(w, precision: int, stream=None, dense_matrix=None) -> Operator:
+    """Create an operator for a workloads.Workload and set its frequencies."""
+    if type(w.system).__name__ == "Dense":
+        d, keep = desc_dense(dense_matrix, w.dt, precision)
+    else:
+        d, keep = desc_for(w.system, w.dt, precision)
+    op = rsv_create_operator(d, stream, keep)
+    rsv_set_frequencies(op, w.omegas)
+    return op
+
+
+def march_opts_for(w, tile_steps: int = 0) -> dict:
+    return dict(variant=w.variant, n_transient_windows=w.n_transient_windows, tail_steps=w.tail_steps,
+                tile_steps=tile_steps)
