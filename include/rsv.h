@@ -152,6 +152,29 @@ rsv_status rsv_march_direct(rsv_operator op, const void* f_hat, int32_t k, const
 rsv_status rsv_march_adjoint(rsv_operator op, const void* y_hat, int32_t k, const rsv_march_opts* opts,
                              void* w_hat);
 
+/* Size in bytes of the fixed device array rsv_march_direct_static works in. */
+#define RSV_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* rsv_march_direct without any device allocation.  The paper has no
+ * counterpart: this is a service to callers that cannot allocate device
+ * memory once running - a host solver that gives the library a fixed memory
+ * budget at start-up, a thread recording into a CUDA stream capture, a
+ * real-time loop that must not wait on the allocator.  rsv_march_direct
+ * grows the operator's workspace on demand; this entry point instead keeps
+ * the march's scratch (state, forcing and snapshot tiles, FP64
+ * accumulators) in one static device array of RSV_STATIC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  Arguments
+ * and result are those of rsv_march_direct (same y_hat to rounding).  The
+ * tile length is halved until the scratch fits; if it cannot fit,
+ * RSV_ERR_INVALID_ARG names the bytes needed.  All calls share the array and
+ * each clears what must start at zero; calls whose device work overlaps
+ * race on it.  The first call on a device takes the array's device address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture begins.  The operator and its frequencies must already exist
+ * (rsv_create_operator / rsv_set_frequencies allocate). */
+rsv_status rsv_march_direct_static(rsv_operator op, const void* f_hat, int32_t k, const rsv_march_opts* opts,
+                                   void* y_hat);
+
 /* Randomized SVD of R_h(w_j) for every frequency (Sec. 1 cites it; App. A for
  * the power iteration it generalises): Y = R Omega, n_power_iter times
  * {Q = qr(Y), Z = R^H Q, Q = qr(Z), Y = R Q}, Q = qr(Y), W = R^H Q, and the

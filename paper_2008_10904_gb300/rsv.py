@@ -67,6 +67,8 @@ _ENTRY_POINTS = {
                                         ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
     "rsv_march_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
+    "rsv_march_direct_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                               ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
     "rsv_gains_modes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.POINTER(rsv_march_opts),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p]),
@@ -178,6 +180,12 @@ def rsv_march_direct(op: Operator, f_hat, k: int, y_hat, **opts):
 def rsv_march_adjoint(op: Operator, y_hat, k: int, w_hat, **opts):
     o = _opts(**opts)
     _check(_lib.rsv_march_adjoint(op.handle, _ptr(y_hat), int(k), ctypes.byref(o), _ptr(w_hat)))
+
+
+def rsv_march_direct_static(op: Operator, f_hat, k: int, y_hat, **opts):
+    """rsv_march_direct with its scratch in the library's static device array (allocates nothing)."""
+    o = _opts(**opts)
+    _check(_lib.rsv_march_direct_static(op.handle, _ptr(f_hat), int(k), ctypes.byref(o), _ptr(y_hat)))
 
 
 def rsv_gains_modes(op: Operator, omega_block, k: int, n_power_iter: int, n_modes: int, gains: np.ndarray,

@@ -19,6 +19,8 @@ def rsv():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    from paper_2008_10904_gb300 import build
     from paper_2008_10904_gb300 import rsv as lib
+    build.build()
     lib.load()
     return lib
