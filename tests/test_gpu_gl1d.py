@@ -96,7 +96,7 @@ def test_march_fp32_matches_oracle(rsv, adjoint):
 
 def test_batched_instances_match_oracle(rsv):
     sysm = W.GL1D(n=(33, 70, 130, 17), mu0=(0.0, -0.1, 0.05, -0.2), x0=-20.0, x1=20.0)
-    w = W.Workload("batch", sysm, np.linspace(-1.0, 1.0, 6), 0.05, 2, "ssrm", n_transient_windows=3)
+    w = W.Workload("batch", sysm, np.linspace(-1.0, 1.0, 6), 0.02, 2, "ssrm", n_transient_windows=3)
     op = rsv.create_for_workload(w, rsv.RSV_PREC_FP64)
     try:
         fh = W.test_block(w)
