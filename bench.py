@@ -316,7 +316,7 @@ def run_ours(args):
 
     # accuracy: the timed path's gains against the FP64 path (itself parity-tested against the oracle)
     acc = None
-    if prec_name != "fp64" and not args.skip_accuracy:
+    if prec_name != "fp64" and not args.skip_accuracy and dense is None:
         op64 = rsv.create_for_workload(w, rsv.RSV_PREC_FP64, stream=stream.cuda_stream, dense_matrix=dense)
         g64 = np.zeros_like(gains)
         rsv.rsv_gains_modes(op64, omega_dev.to(torch.complex128), w.k, w.n_power_iter, w.n_modes, g64, **opts)
@@ -394,7 +394,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(W.ALL), default="c1")
+    ap.add_argument("--workload", choices=sorted(W.ALL), default="c2")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default=None)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -32,12 +32,12 @@ __global__ void __launch_bounds__(kTPB) synth_kernel(TileGeom g, const cpx<R>* _
                                                      const float* __restrict__ cw, void* __restrict__ Fout) {
   extern __shared__ unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);  // [kTauChunk][n_omega]
-  const int n_tau = 2 * g.steps + 1;
+  const int n_tau = g.n_tau > 0 ? g.n_tau : 2 * g.steps + 1;
   const int tau0 = blockIdx.y * kTauChunk;
   const int nt = min(kTauChunk, n_tau - tau0);
   for (int e = threadIdx.x; e < nt * g.n_omega; e += blockDim.x) {
     const int t = e / g.n_omega, j = e - t * g.n_omega;
-    const int64_t q = phase_index(g.sgn * pj[j], 2 * g.n0 + tau0 + t, g.m4);
+    const int64_t q = phase_index(g.sgn * pj[j], 2 * g.n0 + (int64_t)(tau0 + t) * g.tau_stride, g.m4);
     cpx<R> v = tw[q];
     if (REAL) v = R(cw[j]) * v;
     stw[t * g.n_omega + j] = v;
@@ -137,7 +137,7 @@ __global__ void finish_kernel(const cpx<double>* __restrict__ acc, int64_t acc_s
 template <typename R>
 cudaError_t launch_synth(const TileGeom& g, const void* fhat, const void* tw, const int64_t* pj, const float* cw,
                          bool real_state, void* F, cudaStream_t st) {
-  const int n_tau = 2 * g.steps + 1;
+  const int n_tau = g.n_tau > 0 ? g.n_tau : 2 * g.steps + 1;
   dim3 grid((unsigned)((g.rows + kTPB - 1) / kTPB), (unsigned)((n_tau + kTauChunk - 1) / kTauChunk));
   const size_t smem = sizeof(cpx<R>) * kTauChunk * g.n_omega;
   if (real_state) {

@@ -169,6 +169,8 @@ extern "C" rsv_status rsv_march_direct_static(rsv_operator op, const void* f_hat
   using namespace rsv;
   if (!op || !f_hat || !y_hat || k < 1) return fail(RSV_ERR_INVALID_ARG, "bad march arguments");
   if (!op->have_freq) return fail(RSV_ERR_STATE, "rsv_set_frequencies must come first");
+  if (op->kind != RSV_OP_GL1D)
+    return fail(RSV_ERR_INVALID_ARG, "rsv_march_direct_static supports the three-point (GL1D) operator kind only");
   if (f_hat == y_hat) return fail(RSV_ERR_INVALID_ARG, "input and output blocks must not alias");
   return op->prec == RSV_PREC_FP64 ? march_static_impl<double>(op, f_hat, k, opts, y_hat)
                                    : march_static_impl<float>(op, f_hat, k, opts, y_hat);

@@ -79,9 +79,6 @@ rsv_status build_gl1d(rsv_operator op, const rsv_operator_desc* d) {
   return RSV_OK;
 }
 
-rsv_status build_dense(rsv_operator op, const rsv_operator_desc* d) {
-  return fail(RSV_ERR_INVALID_ARG, "dense operator kind is not built in this library version");
-}
 rsv_status build_adr2d(rsv_operator op, const rsv_operator_desc* d) {
   return fail(RSV_ERR_INVALID_ARG, "ADR2D operator kind is not built in this library version");
 }
@@ -93,7 +90,61 @@ int default_tile_steps(rsv_operator op) { return 256; }
 
 int march_group_size(rsv_operator op, int k, int S) { return k; }
 
-size_t stage_scratch_bytes(rsv_operator op, int kg) { return 0; }
+static size_t elem_size(rsv_operator op) { return op->prec == RSV_PREC_FP64 ? 8 : 4; }
+
+// Extra march scratch that lives behind the state vector in the state workspace.
+size_t stage_scratch_bytes(rsv_operator op, int kg) {
+  if (op->kind == RSV_OP_DENSE) return (size_t)kg * op->n * 2 * elem_size(op);  // second state buffer
+  return 0;
+}
+
+rsv_status on_frequencies(rsv_operator op) {
+  if (op->kind == RSV_OP_DENSE) return dense_on_frequencies(op);
+  return RSV_OK;
+}
+
+template <typename R>
+rsv_status prepare_coefficients(rsv_operator op, const void* fhat, int64_t f_stride, int kg, bool adjoint,
+                                const void** coef, int64_t* coef_stride, int* synth_stride) {
+  if (op->kind != RSV_OP_DENSE) {
+    *coef = fhat;
+    *coef_stride = f_stride;
+    *synth_stride = 1;
+    return RSV_OK;
+  }
+  const size_t bytes = (size_t)op->n_omega * kg * op->n * sizeof(cpx<R>);
+  rsv_status s = ensure(op->ws_coef, bytes);
+  if (s == RSV_OK) s = ensure(op->ws_coef2, bytes);
+  if (s != RSV_OK) return s;
+  cudaError_t e = dense_prepare<R>(op, fhat, f_stride, kg, adjoint, op->ws_coef.ptr, op->ws_coef2.ptr);
+  if (e != cudaSuccess) return cuda_fail(e, "dense coefficient transform");
+  *coef = op->ws_coef.ptr;
+  *coef_stride = (int64_t)kg * op->n;
+  *synth_stride = 2;
+  return RSV_OK;
+}
+
+namespace {
+template <typename T>
+__global__ void finite_kernel(const T* __restrict__ x, int64_t count, int* flag) {
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)x[e];
+    if (!(fabs(v) < 1e300)) bad = true;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+}  // namespace
+
+cudaError_t check_finite(rsv_operator op, const void* state, int64_t count, bool real_state) {
+  const int64_t vals = real_state ? count : 2 * count;
+  const unsigned blocks = (unsigned)std::min<int64_t>((vals + 255) / 256, 4 * std::max(op->sm_count, 1));
+  if (op->prec == RSV_PREC_FP64)
+    finite_kernel<double><<<blocks, 256, 0, op->stream>>>((const double*)state, vals, op->d_flag);
+  else
+    finite_kernel<float><<<blocks, 256, 0, op->stream>>>((const float*)state, vals, op->d_flag);
+  return cudaGetLastError();
+}
 
 static Gl1dTile gl1d_geom(rsv_operator op, bool adjoint, int kg) {
   Gl1dTile g;
@@ -126,6 +177,22 @@ cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const v
       g.y_first = t.y_first;
       return launch_gl1d_tile<R>(g, state, F, Y, norms, op->d_flag, op->stream);
     }
+    case RSV_OP_DENSE: {
+      const size_t half = (size_t)t.kg * op->n * sizeof(cpx<R>);
+      char* buf = static_cast<char*>(state);
+      cudaError_t e = cudaSuccess;
+      for (int s = 0; s < t.steps && e == cudaSuccess; ++s) {
+        const int64_t n = t.n0 + s;
+        const bool forced = F != nullptr && n < t.n_forced;
+        void* uin = buf + (size_t)(n & 1) * half;
+        void* uout = buf + (size_t)((n + 1) & 1) * half;
+        const void* f = forced ? static_cast<const char*>(F) + (size_t)s * half : nullptr;
+        void* y = (Y != nullptr && s >= t.y_first) ? static_cast<char*>(Y) + (size_t)s * half : nullptr;
+        e = dense_step<R>(op, t.kg, t.adjoint, uin, uout, f, y);
+      }
+      if (e == cudaSuccess) e = check_finite(op, buf + (size_t)((t.n0 + t.steps) & 1) * half, (int64_t)t.kg * op->n, false);
+      return e;
+    }
     default:
       return cudaErrorNotSupported;
   }
@@ -138,6 +205,8 @@ cudaError_t apply_op(rsv_operator op, const void* x, int k, bool adjoint, void* 
       Gl1dTile g = gl1d_geom(op, adjoint, k);
       return launch_gl1d_apply<R>(g, (const int32_t*)op->d_inst_of_point, x, y, op->stream);
     }
+    case RSV_OP_DENSE:
+      return dense_apply<R>(op, x, k, adjoint, y);
     default:
       return cudaErrorNotSupported;
   }
@@ -145,6 +214,10 @@ cudaError_t apply_op(rsv_operator op, const void* x, int k, bool adjoint, void* 
 
 template cudaError_t march_tile<double>(rsv_operator, const MarchTile&, void*, const void*, void*, double*);
 template cudaError_t march_tile<float>(rsv_operator, const MarchTile&, void*, const void*, void*, double*);
+template rsv_status prepare_coefficients<double>(rsv_operator, const void*, int64_t, int, bool, const void**,
+                                                 int64_t*, int*);
+template rsv_status prepare_coefficients<float>(rsv_operator, const void*, int64_t, int, bool, const void**,
+                                                int64_t*, int*);
 template cudaError_t apply_op<double>(rsv_operator, const void*, int, bool, void*);
 template cudaError_t apply_op<float>(rsv_operator, const void*, int, bool, void*);
 

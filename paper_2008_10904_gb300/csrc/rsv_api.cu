@@ -310,6 +310,11 @@ extern "C" rsv_status rsv_set_frequencies(rsv_operator op, const double* omega, 
   op->n_t = n_t;
   op->h = period / (double)n_t;
   op->have_freq = true;
+  rsv_status ks = on_frequencies(op);
+  if (ks != RSV_OK) {
+    op->have_freq = false;
+    return ks;
+  }
   if (n_steps_per_window) *n_steps_per_window = n_t;
   if (h_out) *h_out = op->h;
   return RSV_OK;
@@ -385,10 +390,19 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
     g.n_omega = op->n_omega;
     g.sgn = adjoint ? -1 : 1;
     g.m4 = 4 * op->n_t;
-    const void* fh = static_cast<const char*>(in) + (size_t)v0 * n * ce;
+    const void* fh = nullptr;
+    int synth_stride = 1;
+    {
+      ProfScope ps(op, PROF_GLUE);
+      st = prepare_coefficients<R>(op, static_cast<const char*>(in) + (size_t)v0 * n * ce, (int64_t)k * n, kv, adjoint,
+                                   &fh, &g.coef_stride, &synth_stride);
+    }
+    if (st != RSV_OK) return st;
+    g.tau_stride = synth_stride;
     for (int64_t n0 = 0; n0 < sc.total; n0 += S) {
       g.n0 = n0;
       g.steps = (int)std::min<int64_t>(S, sc.total - n0);
+      g.n_tau = synth_stride == 2 ? g.steps : 0;
       const bool forced = n0 < sc.forced;
       const bool analysed = n0 + g.steps > sc.first;
       if (forced) {

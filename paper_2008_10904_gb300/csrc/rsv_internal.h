@@ -116,8 +116,12 @@ struct rsv_operator_s {
   // GL1D: tridiagonal coefficients, direct then adjoint: lo, di, up
   void* tri[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int gl_max_n = 0;
-  // DENSE: A and A^H, row-major, element type of the precision
+  // DENSE: A (FP64), A and A^H in the element type, and the RK4 propagator
+  // blocks D, P1, P2, D^H, P1^H, P2^H (element type) for the step dense_h
+  void* dense64[1] = {nullptr};
   void* dense[2] = {nullptr, nullptr};
+  void* prop[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double dense_h = 0.0;
   // stencil kinds: base-flow fields
   void* fld[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double c_dx = 0, c_dy = 0, c_dz = 0;
@@ -126,6 +130,7 @@ struct rsv_operator_s {
 
   // march workspace (grown on demand)
   rsv::Workspace ws_state, ws_ftile, ws_ysnap, ws_acc, ws_norm, ws_glue_a, ws_glue_b, ws_gram, ws_small;
+  rsv::Workspace ws_coef, ws_coef2;
   int* d_flag = nullptr;
   rsv::Profiler prof;
 
@@ -157,9 +162,11 @@ struct TileGeom {
   int steps;           // steps in the tile
   int sgn;             // +1 direct, -1 adjoint (frequencies negated)
   int64_t m4;          // 4 N_T
+  int n_tau = 0;       // synthesis points (0: 2 * steps + 1, the RK4 stage times)
+  int tau_stride = 1;  // half steps between synthesis points
 };
 
-// F[tau][r] = sum_j c_j x(table[q_j(2 n0 + tau)] * fhat[j][r]), tau = 0..2*steps
+// F[tau][r] = sum_j c_j x(table[q_j(2 n0 + tau * tau_stride)] * fhat[j][r]), tau < n_tau
 template <typename R>
 cudaError_t launch_synth(const TileGeom& g, const void* fhat, const void* tw, const int64_t* pj,
                          const float* cw, bool real_state, void* F, cudaStream_t st);

@@ -28,6 +28,29 @@ size_t stage_scratch_bytes(rsv_operator op, int kg);
 template <typename R>
 cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const void* F, void* Y, double* norms);
 
+// Coefficients the synthesis reads for one vector group: the input block itself
+// (stage-based kinds) or a per-march transform of it (dense kind).  Sets
+// *coef / *coef_stride / *n_tau_per_step.
+template <typename R>
+rsv_status prepare_coefficients(rsv_operator op, const void* fhat, int64_t f_stride, int kg, bool adjoint,
+                                const void** coef, int64_t* coef_stride, int* synth_stride);
+
+// Kind-specific work when the frequency grid (and so the step h) changes.
+rsv_status on_frequencies(rsv_operator op);
+
+// Sets the flag if the state block holds a NaN / Inf (kinds without an in-kernel norm monitor).
+cudaError_t check_finite(rsv_operator op, const void* state, int64_t count, bool real_state);
+
+// dense kind (dense_kernels.cu)
+rsv_status dense_on_frequencies(rsv_operator op);
+template <typename R>
+cudaError_t dense_prepare(rsv_operator op, const void* fhat, int64_t f_stride, int kg, bool adjoint, void* out,
+                          void* tmp);
+template <typename R>
+cudaError_t dense_step(rsv_operator op, int kg, bool adjoint, const void* uin, void* uout, const void* F, void* Y);
+template <typename R>
+cudaError_t dense_apply(rsv_operator op, const void* x, int k, bool adjoint, void* y);
+
 // y = A x or A^H x for k vectors.
 template <typename R>
 cudaError_t apply_op(rsv_operator op, const void* x, int k, bool adjoint, void* y);

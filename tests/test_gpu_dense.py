@@ -1,0 +1,148 @@
+"""GPU parity of the dense-operator path (spectral Ginzburg-Landau) against the FP64 oracle.
+
+The CUDA path steps the exact RK4 map as one dense propagator product per
+step; the oracle runs the four RK4 stages.  Both are the same discrete map,
+so the FP64 path must agree to 1e-10.  At the full workload size
+(n = 1024, 256 frequencies, k = 32, TRM over 120111 steps) the oracle's
+march is out of reach, so sampled frequencies are checked against the
+closed-form RK4 resolvent R_h(w) (which the oracle march reaches, pinned in
+tests/test_oracle_pins.py) one frequency at a time.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import frequencies, march, resolvent, rsvd
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32_MARCH = 2e-5
+TOL32_GAIN = 1e-4
+
+
+def _small(variant="ssrm", k=3, n_omega=8, q=1):
+    sysm = W.Dense(n=48, x_half_width=20.0)
+    return W.Workload("dense_small", sysm, np.linspace(-1.0, 1.0, n_omega), 0.02, k, variant,
+                      n_transient_windows=4, tail_steps=2200, n_power_iter=q, n_modes=3)
+
+
+def _dev(x, prec):
+    import torch
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dt)
+
+
+def _relerr(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _oracle(w, a, fh, adjoint=False):
+    g = frequencies.make_grid(w.omegas, w.dt)
+    return march.march(a, g, fh, variant=w.variant, n_trans=w.n_transient_windows, tail_steps=w.tail_steps,
+                       adjoint=adjoint)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_dense_apply(rsv, prec, adjoint):
+    w = _small()
+    a = W.hermite_gl_matrix(w.system)
+    op = rsv.create_for_workload(w, prec, dense_matrix=a)
+    try:
+        x = W.gaussian_block(5, 1, 5, 48)[0]
+        y = _dev(x, prec) * 0
+        rsv.rsv_apply_operator(op, _dev(x, prec), 5, adjoint, y)
+        ref = ((a.conj().T if adjoint else a) @ x.T).T
+        assert _relerr(y.cpu().numpy(), ref) < (1e-13 if prec == 0 else 1e-6)
+    finally:
+        rsv.rsv_destroy_operator(op)
+
+
+@pytest.mark.parametrize("variant,tile", [("ssrm", 64), ("ssrm", 100), ("trm", 256), ("trm", 7)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_dense_march_fp64(rsv, variant, tile, adjoint):
+    w = _small(variant)
+    a = W.hermite_gl_matrix(w.system)
+    op = rsv.create_for_workload(w, 0, dense_matrix=a)
+    try:
+        fh = W.test_block(w)
+        x = _dev(fh, 0)
+        y = x * 0
+        f = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
+        f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=tile))
+        assert _relerr(y.cpu().numpy(), _oracle(w, a, fh, adjoint)) < TOL64
+    finally:
+        rsv.rsv_destroy_operator(op)
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_dense_march_fp32(rsv, adjoint):
+    w = _small("trm", k=4)
+    a = W.hermite_gl_matrix(w.system)
+    op = rsv.create_for_workload(w, 1, dense_matrix=a)
+    try:
+        fh = W.test_block(w).astype(np.complex64).astype(np.complex128)
+        x = _dev(fh, 1)
+        y = x * 0
+        f = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
+        f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=128))
+        assert _relerr(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh, adjoint)) < TOL32_MARCH
+    finally:
+        rsv.rsv_destroy_operator(op)
+
+
+def test_dense_rsvd_fp64(rsv):
+    w = _small("ssrm", k=4, q=2)
+    a = W.hermite_gl_matrix(w.system)
+    op = rsv.create_for_workload(w, 0, dense_matrix=a)
+    try:
+        fh = W.test_block(w)
+        gains = np.zeros((1, w.n_omega, 3))
+        rsv.rsv_gains_modes(op, _dev(fh, 0), w.k, w.n_power_iter, 3, gains, **rsv.march_opts_for(w, 128))
+        g = frequencies.make_grid(w.omegas, w.dt)
+        kw = dict(variant=w.variant, n_trans=w.n_transient_windows, tail_steps=w.tail_steps)
+        rg, _, _ = rsvd.block_rsvd(lambda b: march.march(a, g, b, **kw),
+                                   lambda b: march.march(a, g, b, adjoint=True, **kw), fh, w.n_power_iter, 3)
+        assert np.abs(gains - rg).max() / rg.max() < TOL64
+    finally:
+        rsv.rsv_destroy_operator(op)
+
+
+def _closed_form_rsvd(a, h, om, omega_j, q, n_modes):
+    """The randomized SVD of one frequency with the action R_h(w) applied in closed form."""
+    rh = resolvent.rk4_discrete(a, om, h)
+    block = omega_j[None]
+    md = lambda b: (rh @ b[0].T).T[None]
+    ma = lambda b: (rh.conj().T @ b[0].T).T[None]
+    gains, _, _ = rsvd.block_rsvd(md, ma, block, q, n_modes)
+    return gains[0, 0], rh
+
+
+@pytest.mark.slow
+def test_dense_full_size_sampled(rsv):
+    """Full spectral-GL workload: FP32 march and rSVD gains at sampled frequencies vs closed form."""
+    import torch
+    w = W.dense_hermite_c2()
+    a = W.hermite_gl_matrix(w.system)
+    op = rsv.create_for_workload(w, 1, dense_matrix=a)
+    try:
+        h = frequencies.make_grid(w.omegas, w.dt).h
+        fh = W.test_block(w)
+        x = _dev(fh, 1)
+        gains = np.zeros((1, w.n_omega, 3))
+        rsv.rsv_gains_modes(op, x, w.k, w.n_power_iter, 3, gains, **rsv.march_opts_for(w))
+        for j in (0, 77, 128, 255):
+            ref, rh = _closed_form_rsvd(a, h, w.omegas[j], fh[j].astype(np.complex64).astype(np.complex128),
+                                        w.n_power_iter, 3)
+            err = np.abs(gains[0, j] - ref) / ref
+            assert err.max() < TOL32_GAIN, (j, gains[0, j], ref)
+        # one direct march, element-wise at a sampled frequency
+        y = torch.empty_like(x)
+        rsv.rsv_march_direct(op, x, w.k, y, **rsv.march_opts_for(w))
+        j = 100
+        rh = resolvent.rk4_discrete(a, w.omegas[j], h)
+        ref = (rh @ fh[j].astype(np.complex64).astype(np.complex128).T).T
+        assert _relerr(y[j].cpu().numpy().astype(np.complex128), ref) < 1e-4
+    finally:
+        rsv.rsv_destroy_operator(op)
