@@ -255,6 +255,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     op = rsv.create_for_workload(w, prec, stream=stream.cuda_stream, dense_matrix=dense)
     n_t, h = rsv.rsv_set_frequencies(op, w.omegas)
+    path = rsv.rsv_describe(op)
     opts = rsv.march_opts_for(w, tile_steps=args.tile)
     omega_host = W.test_block(w, seed_offset=rank_seed_offset(rank))
     omega_dev = torch.from_numpy(omega_host).to(device="cuda", dtype=cdt)
@@ -342,7 +343,7 @@ def run_ours(args):
                    "marches_per_step": marches_per_step(w), "actions_per_step": actions_per_step(w),
                    "power_iterations": w.n_power_iter, "precision": prec_name,
                    "l2": "flushed between steps (512 MiB write outside the timed events)",
-                   "parallelism": f"independent replicas x{ws}"},
+                   "parallelism": f"independent replicas x{ws}", "path": path},
         "e2e": {"value": e2e_value, "unit": "actions/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "kernel_ms": {c: {"launches": v[0], "ms": v[1]} for c, v in prof.items()},

@@ -203,6 +203,11 @@ rsv_status rsv_profile_enable(rsv_operator op, int32_t enable);
 rsv_status rsv_profile_reset(rsv_operator op);
 rsv_status rsv_profile_read(rsv_operator op, int32_t category, int64_t* launches, double* ms);
 
+/* One-line description of the operator's execution path (kernels chosen for
+ * this GPU, e.g. the dense step's tensor-core variant and cluster capacity),
+ * written NUL-terminated into buf (host, buflen bytes). */
+rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen);
+
 /* Message of the calling thread's last failing call ("" if none). */
 const char* rsv_last_error(void);
 

@@ -267,8 +267,14 @@ rsv_status dense_on_frequencies(rsv_operator op) {
   combo_kernel<<<blocks, 256, 0, st>>>(n, 2.0, B, 0.5, B2, 0, nullptr, 4.0, T);
   store(T, 2);
   if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    for (auto q : tmp) cudaFree(q);
+    return cuda_fail(e, "propagator build");
+  }
+  rsv_status ts = dense_tc_prepare(op, Dm);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   for (auto q : tmp) cudaFree(q);
+  if (ts != RSV_OK) return ts;
   if (e != cudaSuccess) return cuda_fail(e, "propagator build");
   op->dense_h = op->h;
   return RSV_OK;

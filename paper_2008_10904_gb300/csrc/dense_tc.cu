@@ -1,0 +1,507 @@
+// Tensor-core (tcgen05) RK4 step of the dense propagator, FP32 mode.
+//
+//   u_{n+1} = u_n + D u_n + F_n      (D = RK4 step polynomial minus identity, see dense_kernels.cu)
+//
+// D u is computed as the real GEMM  [Dr; Di] (2n x n)  x  [Ur | Ui] (n x 2kg):
+// rows 0..63 of a CTA's A tile are 64 rows of Re D, rows 64..127 the same rows
+// of Im D, and  Re(Du) = DrUr - DiUi,  Im(Du) = DrUi + DiUr.  Operands are
+// split into TF32 pairs (x = hi + lo, hi = tf32(x)) and three MMAs
+// (hi*hi + hi*lo + lo*hi) give FP32-level products with FP32 accumulation in
+// tensor memory.
+//
+// Grid: one cluster of CS = n/128 CTAs per block of 64 complex rows; CTA rank
+// j of a cluster owns the K slice of 128 complex columns [128 j, 128 j + 128).
+// Each CTA bulk-copies its pre-arranged A tile (hi, lo: 2 x 64 KB) and its X
+// slice (hi, lo: 2 x 32 KB) into shared memory, issues 16 K-steps x 3 MMAs
+// (M = 128, N = 64, K = 8) from one thread, reads the 128 x 64 partial from
+// tensor memory and exchanges it through distributed shared memory: CTA j
+// sums over the cluster the partials of its 64/CS complex rows (stacked rows
+// r and 64 + r) and
+// writes the new state, the snapshot, and the TF32 split of the new state
+// in the operand layout of the next step.  All waits are bounded; a timeout
+// sets the error flag.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+
+#include "rsv_ops.h"
+#include "tc_ptx.h"
+
+namespace rsv {
+namespace {
+
+constexpr int kTileK = 128;                         // complex columns per K slice
+constexpr int kTileRows = 64;                       // complex rows per cluster
+constexpr int kM = 128, kN = 64;                    // MMA shape (real rows, 2 x 32 vector columns)
+constexpr uint32_t kATileFloats = kM * kTileK;      // 16384 floats = 64 KB
+constexpr uint32_t kXTileFloats = kN * kTileK;      // 8192 floats = 32 KB
+constexpr uint32_t kSmemBytes = 4 * kATileFloats + 4 * kATileFloats + 4 * kXTileFloats + 4 * kXTileFloats + 64;
+constexpr uint32_t kWaitTries = 1u << 24;
+constexpr int kRedLd = kN + 1;
+
+struct TcStepArgs {
+  const float* A;     // [n/64][CS][2][kATileFloats]
+  const float* Xin;   // [CS][2][kXTileFloats]
+  float* Xout;
+  const cpx<float>* uin;   // [kg][n]
+  cpx<float>* uout;
+  const cpx<float>* F;     // nullable
+  cpx<float>* Y;           // nullable
+  int n, kg, cs;
+  int* err;
+};
+
+__global__ void __launch_bounds__(256, 1) dense_tc_step_kernel(TcStepArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* A_hi = reinterpret_cast<float*>(smem);
+  float* A_lo = A_hi + kATileFloats;
+  float* X_hi = A_lo + kATileFloats;
+  float* X_lo = X_hi + kXTileFloats;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(X_lo + kXTileFloats);  // [0] loads, [1] mma
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 2);
+  float* red = A_hi;  // reused for the 128 x 64 partial once the MMAs have completed
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t mb = tc::cluster_id_x();
+  const uint32_t j = tc::cluster_rank();
+  if (tid == 0) {
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tbase, 64);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tbase;
+
+  if (tid == 0) {
+    const float* at = a.A + ((size_t)mb * a.cs + j) * 2 * kATileFloats;
+    const float* xt = a.Xin + (size_t)j * 2 * kXTileFloats;
+    tc::mbar_arrive_expect_tx(&bars[0], 4 * (2 * kATileFloats + 2 * kXTileFloats));
+    tc::bulk_g2s(A_hi, at, 4 * kATileFloats, &bars[0]);
+    tc::bulk_g2s(A_lo, at + kATileFloats, 4 * kATileFloats, &bars[0]);
+    tc::bulk_g2s(X_hi, xt, 4 * kXTileFloats, &bars[0]);
+    tc::bulk_g2s(X_lo, xt + kXTileFloats, 4 * kXTileFloats, &bars[0]);
+  }
+  bool ok = tc::mbar_wait(&bars[0], 0, kWaitTries);
+  if (tid == 0) {
+    if (ok) {
+      const uint32_t idesc = tc::idesc_tf32(kM, kN);
+      const uint32_t lbo = 128, sbo_a = (kTileK / 4) * 128, sbo_x = (kTileK / 4) * 128;
+#pragma unroll 1
+      for (int ks = 0; ks < kTileK / 8; ++ks) {
+        const uint64_t ah = tc::smem_desc(reinterpret_cast<char*>(A_hi) + ks * 256, lbo, sbo_a);
+        const uint64_t al = tc::smem_desc(reinterpret_cast<char*>(A_lo) + ks * 256, lbo, sbo_a);
+        const uint64_t xh = tc::smem_desc(reinterpret_cast<char*>(X_hi) + ks * 256, lbo, sbo_x);
+        const uint64_t xl = tc::smem_desc(reinterpret_cast<char*>(X_lo) + ks * 256, lbo, sbo_x);
+        tc::mma_tf32(tmem, ah, xh, idesc, ks > 0);
+        tc::mma_tf32(tmem, ah, xl, idesc, true);
+        tc::mma_tf32(tmem, al, xh, idesc, true);
+      }
+      tc::mma_commit(&bars[1]);
+    } else {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bars[1])) : "memory");
+    }
+  }
+  ok = tc::mbar_wait(&bars[1], 0, kWaitTries) && ok;
+  tc::tc_fence_after();
+  if (warp < 4) {
+    const int row = 32 * warp + lane;
+#pragma unroll
+    for (int c = 0; c < kN; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) red[row * kRedLd + c + q] = ok ? v[q] : 0.f;
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::cluster_sync();
+
+  // cluster reduction + RK4 update: CTA j owns complex rows [rpc j, rpc j + rpc) of the
+  // cluster's 64-row block (rpc = 64 / cs), i.e. stacked rows iloc and 64 + iloc
+  {
+    const int rpc = kTileRows / a.cs;
+    for (int pidx = tid; pidx < rpc * 32; pidx += blockDim.x) {
+      const int ii = pidx >> 5;
+      const int v = pidx & 31;
+      const int iloc = rpc * (int)j + ii;
+      float pr = 0.f, pi = 0.f;
+      {
+        float rr[8], ri[8], ir[8], ix[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          if (p < a.cs) {
+            rr[p] = tc::ld_peer_f32(tc::map_peer(&red[iloc * kRedLd + v], p));
+            ri[p] = tc::ld_peer_f32(tc::map_peer(&red[iloc * kRedLd + 32 + v], p));
+            ir[p] = tc::ld_peer_f32(tc::map_peer(&red[(64 + iloc) * kRedLd + v], p));
+            ix[p] = tc::ld_peer_f32(tc::map_peer(&red[(64 + iloc) * kRedLd + 32 + v], p));
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          if (p < a.cs) {
+            pr += rr[p] - ix[p];
+            pi += ri[p] + ir[p];
+          }
+        }
+      }
+      const int i = (int)mb * kTileRows + iloc;
+      if (v < a.kg && i < a.n) {
+        const int64_t e = (int64_t)v * a.n + i;
+        const cpx<float> u0 = a.uin[e];
+        cpx<float> u1 = mk<float>(u0.re + pr, u0.im + pi);
+        if (a.F) u1 = u1 + a.F[e];
+        a.uout[e] = u1;
+        if (a.Y) a.Y[e] = u0;
+        const int js = i / kTileK, kk = i % kTileK;
+        float* xo = a.Xout + (size_t)js * 2 * kXTileFloats;
+        const float hr = tc::to_tf32(u1.re), hi = tc::to_tf32(u1.im);
+        const uint32_t o_re = tc::kmajor_offset(v, kk, kTileK) / 4, o_im = tc::kmajor_offset(32 + v, kk, kTileK) / 4;
+        xo[o_re] = hr;
+        xo[kXTileFloats + o_re] = u1.re - hr;
+        xo[o_im] = hi;
+        xo[kXTileFloats + o_im] = u1.im - hi;
+      }
+    }
+  }
+  tc::cluster_sync();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+  if (!ok && tid == 0) atomicExch(a.err, 2);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent variant (no clusters): one launch marches a whole time tile with
+// MB * CS CTAs, one per SM, all resident at once.  CTA (mb, j) keeps the A
+// tile of row block mb and K slice j in shared memory for the whole tile.
+// Per step it waits until row blocks 2j and 2j+1 (the producers of its K
+// slice) have published the step, bulk-copies its X slice, runs the MMAs,
+// and adds its 128 x 64 partial into the row block's FP32 accumulator with
+// vector atomics in L2.  The last CTA of the row block to arrive (arrival
+// counter) does the RK4 epilogue for the block's 64 rows, re-zeroes the
+// accumulator and publishes the block's step counter.  Every row block reads
+// all K slices, so no CTA can run more than one step ahead of any other:
+// accumulators, counters and X operands are double-buffered by step parity.
+// Spins are bounded and stop early once any CTA has set the error.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSmemPersistent = 4 * (2 * kATileFloats + 2 * kXTileFloats) + 64;
+constexpr uint32_t kSpinTries = 1u << 24;
+
+struct TcMarchArgs {
+  const float* A;
+  float* X;                 // [2][CS][2][kXTileFloats]
+  float* acc;               // [2][MB][kM][kN]
+  int* cnt;                 // [2][MB]
+  cpx<float>* u;            // [2][kg][n]
+  const cpx<float>* F;      // [steps][kg][n] or null
+  cpx<float>* Y;            // [steps][kg][n] or null
+  int64_t n0;
+  int steps;
+  int64_t n_forced;
+  int y_first;
+  int n, kg, cs;
+  int* ready;               // [MB]
+  int* err;
+};
+
+__global__ void __launch_bounds__(256, 1) dense_tc_march_kernel(TcMarchArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* A_hi = reinterpret_cast<float*>(smem);
+  float* A_lo = A_hi + kATileFloats;
+  float* X_hi = A_lo + kATileFloats;
+  float* X_lo = X_hi + kXTileFloats;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(X_lo + kXTileFloats);  // [0] A, [1] X, [2] MMA
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 3);
+  int* last = reinterpret_cast<int*>(tbase + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int MB = a.n / kTileRows;
+  const int mb = blockIdx.x / a.cs;
+  const int j = blockIdx.x % a.cs;
+  if (tid == 0) {
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+    tc::mbar_init(&bars[2], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tbase, 64);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tbase;
+  if (tid == 0) {
+    const float* at = a.A + ((size_t)mb * a.cs + j) * 2 * kATileFloats;
+    tc::mbar_arrive_expect_tx(&bars[0], 4 * 2 * kATileFloats);
+    tc::bulk_g2s(A_hi, at, 4 * kATileFloats, &bars[0]);
+    tc::bulk_g2s(A_lo, at + kATileFloats, 4 * kATileFloats, &bars[0]);
+  }
+  bool ok = tc::mbar_wait(&bars[0], 0, kWaitTries);
+  const size_t xset = (size_t)a.cs * 2 * kXTileFloats;
+  const int64_t rows = (int64_t)a.kg * a.n;
+  const uint32_t idesc = tc::idesc_tf32(kM, kN);
+  const uint32_t sbo = (kTileK / 4) * 128;
+  volatile int* errv = a.err;
+
+  for (int s = 0; s < a.steps; ++s) {
+    const int64_t n = a.n0 + s;
+    const int par = (int)(n & 1);
+    if (tid == 0) {
+      bool got = false;
+      for (uint32_t it = 0; it < kSpinTries; ++it) {
+        if (*errv != 0) break;
+        if (tc::ld_acquire(&a.ready[2 * j]) >= (int)n && tc::ld_acquire(&a.ready[2 * j + 1]) >= (int)n) {
+          got = true;
+          break;
+        }
+      }
+      if (!got) atomicExch(a.err, 2);
+      tc::fence_proxy_async_global();
+      const float* xt = a.X + (size_t)par * xset + (size_t)j * 2 * kXTileFloats;
+      tc::mbar_arrive_expect_tx(&bars[1], 4 * 2 * kXTileFloats);
+      tc::bulk_g2s(X_hi, xt, 4 * kXTileFloats, &bars[1]);
+      tc::bulk_g2s(X_lo, xt + kXTileFloats, 4 * kXTileFloats, &bars[1]);
+    }
+    ok = tc::mbar_wait(&bars[1], (uint32_t)(s & 1), kWaitTries) && ok;
+    tc::tc_fence_after();
+    if (tid == 0) {
+      if (ok) {
+#pragma unroll 1
+        for (int ks = 0; ks < kTileK / 8; ++ks) {
+          const uint64_t ah = tc::smem_desc(reinterpret_cast<char*>(A_hi) + ks * 256, 128, sbo);
+          const uint64_t al = tc::smem_desc(reinterpret_cast<char*>(A_lo) + ks * 256, 128, sbo);
+          const uint64_t xh = tc::smem_desc(reinterpret_cast<char*>(X_hi) + ks * 256, 128, sbo);
+          const uint64_t xl = tc::smem_desc(reinterpret_cast<char*>(X_lo) + ks * 256, 128, sbo);
+          tc::mma_tf32(tmem, ah, xh, idesc, ks > 0);
+          tc::mma_tf32(tmem, ah, xl, idesc, true);
+          tc::mma_tf32(tmem, al, xh, idesc, true);
+        }
+        tc::mma_commit(&bars[2]);
+      } else {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bars[2])) : "memory");
+      }
+    }
+    ok = tc::mbar_wait(&bars[2], (uint32_t)(s & 1), kWaitTries) && ok;
+    tc::tc_fence_after();
+    float* accb = a.acc + ((size_t)par * MB + mb) * kM * kN;
+    if (warp < 4 && ok) {
+      const int row = 32 * warp + lane;
+#pragma unroll
+      for (int c = 0; c < kN; c += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c, v);
+        float4* dst = reinterpret_cast<float4*>(accb + row * kN + c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+      }
+    }
+    __threadfence();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0) *last = (atomicAdd(&a.cnt[par * MB + mb], 1) == a.cs - 1);
+    __syncthreads();
+    if (*last) {
+      __threadfence();
+      const cpx<float>* uin = a.u + (size_t)par * rows;
+      cpx<float>* uout = a.u + (size_t)(1 - par) * rows;
+      const cpx<float>* Fs = (a.F != nullptr && n < a.n_forced) ? a.F + (size_t)s * rows : nullptr;
+      cpx<float>* Ys = (a.Y != nullptr && s >= a.y_first) ? a.Y + (size_t)s * rows : nullptr;
+      float* xout = a.X + (size_t)(1 - par) * xset;
+      for (int p = tid; p < kTileRows * 32; p += blockDim.x) {
+        const int iloc = p >> 5;
+        const int v = p & 31;
+        const float pr = __ldcg(accb + iloc * kN + v) - __ldcg(accb + (64 + iloc) * kN + 32 + v);
+        const float pi = __ldcg(accb + iloc * kN + 32 + v) + __ldcg(accb + (64 + iloc) * kN + v);
+        const int i = mb * kTileRows + iloc;
+        if (v < a.kg && i < a.n) {
+          const int64_t e = (int64_t)v * a.n + i;
+          const float2 u0 = __ldcg(reinterpret_cast<const float2*>(uin + e));
+          float2 u1 = make_float2(u0.x + pr, u0.y + pi);
+          if (Fs) {
+            const float2 f = __ldcg(reinterpret_cast<const float2*>(Fs + e));
+            u1.x += f.x;
+            u1.y += f.y;
+          }
+          __stcg(reinterpret_cast<float2*>(uout + e), u1);
+          if (Ys) __stcg(reinterpret_cast<float2*>(Ys + e), u0);
+          const int js = i / kTileK, kk = i % kTileK;
+          float* xo = xout + (size_t)js * 2 * kXTileFloats;
+          const float hr = tc::to_tf32(u1.x), hi = tc::to_tf32(u1.y);
+          const uint32_t o_re = tc::kmajor_offset(v, kk, kTileK) / 4, o_im = tc::kmajor_offset(32 + v, kk, kTileK) / 4;
+          __stcg(xo + o_re, hr);
+          __stcg(xo + kXTileFloats + o_re, u1.x - hr);
+          __stcg(xo + o_im, hi);
+          __stcg(xo + kXTileFloats + o_im, u1.y - hi);
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < kM * kN / 4; e += blockDim.x)
+        __stcg(reinterpret_cast<float4*>(accb) + e, make_float4(0.f, 0.f, 0.f, 0.f));
+      tc::fence_proxy_async_global();
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        a.cnt[par * MB + mb] = 0;
+        __threadfence();
+        tc::st_release(&a.ready[mb], (int)(n + 1));
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+  if (!ok && tid == 0) atomicExch(a.err, 2);
+}
+
+// A tiles from the FP64 matrix (conj-transposed for the adjoint): tile (mb, j) rows
+// r < 64: Re M[64 mb + r][128 j + k], r >= 64: Im M[64 mb + r - 64][128 j + k]; hi/lo TF32 split.
+__global__ void arrange_a_kernel(int n, int cs, const cpx<double>* __restrict__ M, bool conj_t, float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over (mb, j, r, k)
+  const int64_t total = (int64_t)(n / kTileRows) * cs * kM * kTileK;
+  if (e >= total) return;
+  const int k = (int)(e % kTileK);
+  const int r = (int)((e / kTileK) % kM);
+  const int j = (int)((e / ((int64_t)kTileK * kM)) % cs);
+  const int mb = (int)(e / ((int64_t)kTileK * kM * cs));
+  const int row = mb * kTileRows + (r & 63), col = j * kTileK + k;
+  const cpx<double> m = conj_t ? conjg(M[(int64_t)col * n + row]) : M[(int64_t)row * n + col];
+  const double x = (r < 64) ? m.re : m.im;
+  const float hi = tc::to_tf32((float)x);
+  const float lo = (float)(x - (double)hi);
+  float* tile = out + ((size_t)mb * cs + j) * 2 * kATileFloats;
+  const uint32_t o = tc::kmajor_offset(r, k, kTileK) / 4;
+  tile[o] = hi;
+  tile[kATileFloats + o] = lo;
+}
+
+}  // namespace
+
+bool dense_tc_supported(rsv_operator op, int kg) {
+  if (op->prec != RSV_PREC_FP32 || op->kind != RSV_OP_DENSE) return false;
+  if (op->tc_disabled) return false;
+  const int n = (int)op->n;
+  if (n % kTileK != 0 || n / kTileK > 8 || kg > 32) return false;
+  return op->tc_tiles[0] != nullptr;
+}
+
+size_t dense_tc_scratch_bytes(rsv_operator op) {
+  return (size_t)2 * (op->n / kTileK) * 2 * kXTileFloats * sizeof(float);
+}
+
+// Build the hi/lo A tiles of D and D^H (after the FP64 propagator build).
+rsv_status dense_tc_prepare(rsv_operator op, const void* d64_direct) {
+  const int n = (int)op->n;
+  if (op->prec != RSV_PREC_FP32 || n % kTileK != 0 || n / kTileK > 8 || op->tc_disabled) return RSV_OK;
+  const int cs = n / kTileK;
+  const size_t floats = (size_t)(n / kTileRows) * cs * 2 * kATileFloats;
+  for (int d = 0; d < 2; ++d) {
+    if (!op->tc_tiles[d]) {
+      cudaError_t e = cudaMalloc(&op->tc_tiles[d], floats * sizeof(float));
+      if (e != cudaSuccess) return cuda_fail(e, "tensor-core tiles");
+      op->dev.push_back(op->tc_tiles[d]);
+    }
+    const int64_t total = (int64_t)(n / kTileRows) * cs * kM * kTileK;
+    arrange_a_kernel<<<(unsigned)((total + 255) / 256), 256, 0, op->stream>>>(
+        n, cs, (const cpx<double>*)d64_direct, d == 1, (float*)op->tc_tiles[d]);
+  }
+  cudaError_t e = cudaFuncSetAttribute(dense_tc_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dense_tc_march_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemPersistent);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core tiles");
+  // The persistent tile kernel needs all of its CTAs resident at once (one per SM).
+  op->tc_persistent = false;
+  const int MB = n / kTileRows;
+  if (!op->d_ready) {
+    e = cudaMalloc(&op->d_ready, sizeof(int) * (MB + 2 * MB));
+    if (e == cudaSuccess) op->dev.push_back(op->d_ready);
+    if (e == cudaSuccess) e = cudaMalloc(&op->tc_acc, sizeof(float) * 2 * MB * kM * kN);
+    if (e == cudaSuccess) op->dev.push_back(op->tc_acc);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core march buffers");
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_tc_march_kernel, 256, kSmemPersistent);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 0;
+  }
+  op->tc_max_clusters = per_sm * op->sm_count;  // resident CTAs
+  const char* env = getenv("RSV_DENSE_PERSISTENT");
+  op->tc_persistent = per_sm * op->sm_count >= MB * cs && !(env != nullptr && env[0] == '0');
+  return RSV_OK;
+}
+
+// A whole tile of steps in one persistent launch (requires op->tc_persistent).
+cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n0, int steps, int64_t n_forced,
+                                int y_first, void* state, const void* F, void* Y, void* xbuf) {
+  const int n = (int)op->n;
+  const int cs = n / kTileK;
+  const int MB = n / kTileRows;
+  TcMarchArgs a;
+  a.A = (const float*)op->tc_tiles[adjoint ? 1 : 0];
+  a.X = (float*)xbuf;
+  a.acc = (float*)op->tc_acc;
+  a.cnt = (int*)op->d_ready + MB;
+  a.u = (cpx<float>*)state;
+  a.F = (const cpx<float>*)F;
+  a.Y = (cpx<float>*)Y;
+  a.n0 = n0;
+  a.steps = steps;
+  a.n_forced = n_forced;
+  a.y_first = y_first;
+  a.n = n;
+  a.kg = kg;
+  a.cs = cs;
+  a.ready = (int*)op->d_ready;
+  a.err = op->d_flag;
+  cudaError_t e = cudaSuccess;
+  if (n0 == 0) {
+    e = cudaMemsetAsync(op->d_ready, 0, sizeof(int) * 3 * MB, op->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(op->tc_acc, 0, sizeof(float) * 2 * MB * kM * kN, op->stream);
+  }
+  if (e != cudaSuccess) return e;
+  dense_tc_march_kernel<<<MB * cs, 256, kSmemPersistent, op->stream>>>(a);
+  return cudaGetLastError();
+}
+
+// One step; xbuf holds two X operand sets (ping-pong by step parity).
+cudaError_t dense_tc_step(rsv_operator op, int kg, bool adjoint, int64_t step, const void* uin, void* uout,
+                          const void* F, void* Y, void* xbuf) {
+  const int n = (int)op->n;
+  const int cs = n / kTileK;
+  const size_t xset = (size_t)cs * 2 * kXTileFloats;
+  TcStepArgs a;
+  a.A = (const float*)op->tc_tiles[adjoint ? 1 : 0];
+  a.Xin = (const float*)xbuf + (size_t)(step & 1) * xset;
+  a.Xout = (float*)xbuf + (size_t)((step + 1) & 1) * xset;
+  a.uin = (const cpx<float>*)uin;
+  a.uout = (cpx<float>*)uout;
+  a.F = (const cpx<float>*)F;
+  a.Y = (cpx<float>*)Y;
+  a.n = n;
+  a.kg = kg;
+  a.cs = cs;
+  a.err = op->d_flag;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((n / kTileRows) * cs), 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = op->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, dense_tc_step_kernel, a);
+}
+
+}  // namespace rsv

@@ -94,7 +94,8 @@ static size_t elem_size(rsv_operator op) { return op->prec == RSV_PREC_FP64 ? 8 
 
 // Extra march scratch that lives behind the state vector in the state workspace.
 size_t stage_scratch_bytes(rsv_operator op, int kg) {
-  if (op->kind == RSV_OP_DENSE) return (size_t)kg * op->n * 2 * elem_size(op);  // second state buffer
+  if (op->kind == RSV_OP_DENSE)  // second state buffer, then the tensor-core operand buffers
+    return (size_t)kg * op->n * 2 * elem_size(op) + (dense_tc_supported(op, kg) ? dense_tc_scratch_bytes(op) : 0);
   return 0;
 }
 
@@ -181,6 +182,12 @@ cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const v
       const size_t half = (size_t)t.kg * op->n * sizeof(cpx<R>);
       char* buf = static_cast<char*>(state);
       cudaError_t e = cudaSuccess;
+      if (sizeof(R) == 4 && dense_tc_supported(op, t.kg) && op->tc_persistent) {
+        e = dense_tc_march_tile(op, t.kg, t.adjoint, t.n0, t.steps, t.n_forced, t.y_first, buf, F, Y, buf + 2 * half);
+        if (e == cudaSuccess)
+          e = check_finite(op, buf + (size_t)((t.n0 + t.steps) & 1) * half, (int64_t)t.kg * op->n, false);
+        return e;
+      }
       for (int s = 0; s < t.steps && e == cudaSuccess; ++s) {
         const int64_t n = t.n0 + s;
         const bool forced = F != nullptr && n < t.n_forced;
@@ -188,7 +195,10 @@ cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const v
         void* uout = buf + (size_t)((n + 1) & 1) * half;
         const void* f = forced ? static_cast<const char*>(F) + (size_t)s * half : nullptr;
         void* y = (Y != nullptr && s >= t.y_first) ? static_cast<char*>(Y) + (size_t)s * half : nullptr;
-        e = dense_step<R>(op, t.kg, t.adjoint, uin, uout, f, y);
+        if (sizeof(R) == 4 && dense_tc_supported(op, t.kg))
+          e = dense_tc_step(op, t.kg, t.adjoint, n, uin, uout, f, y, buf + 2 * half);
+        else
+          e = dense_step<R>(op, t.kg, t.adjoint, uin, uout, f, y);
       }
       if (e == cudaSuccess) e = check_finite(op, buf + (size_t)((t.n0 + t.steps) & 1) * half, (int64_t)t.kg * op->n, false);
       return e;

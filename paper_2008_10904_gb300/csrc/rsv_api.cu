@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -160,6 +161,11 @@ extern "C" rsv_status rsv_create_operator(const rsv_operator_desc* d, void* stre
   op->prec = d->precision;
   op->dt = d->dt;
   op->stream = (cudaStream_t)stream;
+  {
+    // RSV_DENSE_TENSOR=0 keeps dense FP32 operators on the CUDA-core step (for comparisons)
+    const char* env = getenv("RSV_DENSE_TENSOR");
+    op->tc_disabled = env != nullptr && env[0] == '0';
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&op->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -199,6 +205,22 @@ extern "C" void rsv_destroy_operator(rsv_operator op) {
   if (!op) return;
   cudaStreamSynchronize(op->stream);
   delete op;
+}
+
+extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
+  if (!op || !buf || buflen < 1) return fail(RSV_ERR_INVALID_ARG, "bad describe arguments");
+  static const char* kinds[] = {"gl1d", "dense", "adr2d", "adv3d"};
+  const char* path = "cuda-core stages";
+  if (op->kind == RSV_OP_DENSE) {
+    if (op->prec == RSV_PREC_FP32 && op->tc_tiles[0] && !op->tc_disabled)
+      path = op->tc_persistent ? "tcgen05 3xTF32 persistent tile kernel" : "tcgen05 3xTF32 one launch per step";
+    else
+      path = "cuda-core propagator step";
+  }
+  snprintf(buf, (size_t)buflen, "kind=%s precision=%s n=%lld instances=%d path=%s resident_ctas=%d sms=%d",
+           (op->kind >= 0 && op->kind < 4) ? kinds[op->kind] : "?", op->prec == RSV_PREC_FP64 ? "fp64" : "fp32",
+           (long long)op->n, op->n_inst, path, op->tc_max_clusters, op->sm_count);
+  return RSV_OK;
 }
 
 extern "C" rsv_status rsv_operator_info(rsv_operator op, int64_t* n, int32_t* n_instances, int32_t* real_state) {
@@ -382,7 +404,7 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
       acc_stride = rows;
       e = cudaMemsetAsync(acc, 0, (size_t)op->n_omega * rows * sizeof(cpx<double>), stream);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(op->ws_state.ptr, 0, rows * se, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(op->ws_state.ptr, 0, rows * se + stage_scratch_bytes(op, kv), stream);
     if (e != cudaSuccess) return cuda_fail(e, "march reset");
     TileGeom g;
     g.rows = rows;
@@ -439,6 +461,7 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
   e = cudaMemcpyAsync(&flag, op->d_flag, sizeof(int), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(e, "march");
+  if (flag == 2) return fail(RSV_ERR_TIMEOUT, "a bounded device wait expired in the tensor-core step");
   if (flag) return fail(RSV_ERR_DIVERGED, "state norm became non-finite during the march");
   return RSV_OK;
 }

@@ -122,6 +122,13 @@ struct rsv_operator_s {
   void* dense[2] = {nullptr, nullptr};
   void* prop[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double dense_h = 0.0;
+  // tensor-core operand tiles of D and D^H (FP32 mode), and the switch that turns them off
+  void* tc_tiles[2] = {nullptr, nullptr};
+  bool tc_disabled = false;
+  bool tc_persistent = false;   // all clusters of the tile kernel fit on the GPU at once
+  int tc_max_clusters = 0;      // resident CTAs of the persistent tile kernel on this GPU
+  void* d_ready = nullptr;      // per-block step counters and arrival counters of the persistent tile kernel
+  void* tc_acc = nullptr;       // its FP32 partial-sum accumulators
   // stencil kinds: base-flow fields
   void* fld[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double c_dx = 0, c_dy = 0, c_dz = 0;

@@ -51,6 +51,15 @@ cudaError_t dense_step(rsv_operator op, int kg, bool adjoint, const void* uin, v
 template <typename R>
 cudaError_t dense_apply(rsv_operator op, const void* x, int k, bool adjoint, void* y);
 
+// tensor-core dense step (dense_tc.cu)
+bool dense_tc_supported(rsv_operator op, int kg);
+size_t dense_tc_scratch_bytes(rsv_operator op);
+rsv_status dense_tc_prepare(rsv_operator op, const void* d64_direct);
+cudaError_t dense_tc_step(rsv_operator op, int kg, bool adjoint, int64_t step, const void* uin, void* uout,
+                          const void* F, void* Y, void* xbuf);
+cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n0, int steps, int64_t n_forced,
+                                int y_first, void* state, const void* F, void* Y, void* xbuf);
+
 // y = A x or A^H x for k vectors.
 template <typename R>
 cudaError_t apply_op(rsv_operator op, const void* x, int k, bool adjoint, void* y);

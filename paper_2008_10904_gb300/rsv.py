@@ -78,6 +78,7 @@ _ENTRY_POINTS = {
     "rsv_profile_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "rsv_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double)]),
+    "rsv_describe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]),
     "rsv_last_error": (ctypes.c_char_p, []),
     "rsv_version": (ctypes.c_char_p, []),
 }
@@ -219,6 +220,12 @@ def rsv_profile_read(op: Operator, category: int):
     n, ms = ctypes.c_int64(), ctypes.c_double()
     _check(_lib.rsv_profile_read(op.handle, int(category), ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def rsv_describe(op: Operator) -> str:
+    buf = ctypes.create_string_buffer(512)
+    _check(_lib.rsv_describe(op.handle, buf, 512))
+    return buf.value.decode()
 
 
 def rsv_last_error() -> str:
