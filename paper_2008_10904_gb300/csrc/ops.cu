@@ -79,12 +79,6 @@ rsv_status build_gl1d(rsv_operator op, const rsv_operator_desc* d) {
   return RSV_OK;
 }
 
-rsv_status build_adr2d(rsv_operator op, const rsv_operator_desc* d) {
-  return fail(RSV_ERR_INVALID_ARG, "ADR2D operator kind is not built in this library version");
-}
-rsv_status build_adv3d(rsv_operator op, const rsv_operator_desc* d) {
-  return fail(RSV_ERR_INVALID_ARG, "ADV3D operator kind is not built in this library version");
-}
 
 int default_tile_steps(rsv_operator op) { return 256; }
 
@@ -96,6 +90,7 @@ static size_t elem_size(rsv_operator op) { return op->prec == RSV_PREC_FP64 ? 8 
 size_t stage_scratch_bytes(rsv_operator op, int kg) {
   if (op->kind == RSV_OP_DENSE)  // second state buffer, then the tensor-core operand buffers
     return (size_t)kg * op->n * 2 * elem_size(op) + (dense_tc_supported(op, kg) ? dense_tc_scratch_bytes(op) : 0);
+  if (op->kind == RSV_OP_ADR2D || op->kind == RSV_OP_ADV3D) return stencil_scratch_bytes(op, kg);
   return 0;
 }
 
@@ -203,6 +198,9 @@ cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const v
       if (e == cudaSuccess) e = check_finite(op, buf + (size_t)((t.n0 + t.steps) & 1) * half, (int64_t)t.kg * op->n, false);
       return e;
     }
+    case RSV_OP_ADR2D:
+    case RSV_OP_ADV3D:
+      return stencil_march_tile<R>(op, t, state, F, Y);
     default:
       return cudaErrorNotSupported;
   }
@@ -217,6 +215,9 @@ cudaError_t apply_op(rsv_operator op, const void* x, int k, bool adjoint, void* 
     }
     case RSV_OP_DENSE:
       return dense_apply<R>(op, x, k, adjoint, y);
+    case RSV_OP_ADR2D:
+    case RSV_OP_ADV3D:
+      return stencil_apply<R>(op, x, k, adjoint, y);
     default:
       return cudaErrorNotSupported;
   }

@@ -134,6 +134,8 @@ struct rsv_operator_s {
   double c_dx = 0, c_dy = 0, c_dz = 0;
   int nx = 0, ny = 0, nz = 0;
   double visc = 0;
+  int sponge_cells = 0;
+  double sponge_amp = 0;
 
   // march workspace (grown on demand)
   rsv::Workspace ws_state, ws_ftile, ws_ysnap, ws_acc, ws_norm, ws_glue_a, ws_glue_b, ws_gram, ws_small;

@@ -60,6 +60,13 @@ cudaError_t dense_tc_step(rsv_operator op, int kg, bool adjoint, int64_t step, c
 cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n0, int steps, int64_t n_forced,
                                 int y_first, void* state, const void* F, void* Y, void* xbuf);
 
+// structured-grid kinds (stencil_kernels.cu)
+size_t stencil_scratch_bytes(rsv_operator op, int kg);
+template <typename R>
+cudaError_t stencil_march_tile(rsv_operator op, const MarchTile& t, void* state, const void* F, void* Y);
+template <typename R>
+cudaError_t stencil_apply(rsv_operator op, const void* x, int k, bool adjoint, void* y);
+
 // y = A x or A^H x for k vectors.
 template <typename R>
 cudaError_t apply_op(rsv_operator op, const void* x, int k, bool adjoint, void* y);

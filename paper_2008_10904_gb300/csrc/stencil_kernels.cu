@@ -1,0 +1,393 @@
+// Structured-grid operators with real state: the 2-D jet advection-diffusion-
+// reaction system (5-point stencil) and the 3-D three-component linearised
+// advection-diffusion system (7-point stencil), and their RK4 march.
+//
+// Classical RK4 in low-storage form, one fused kernel per stage:
+//   stage 1: k = A u   + f(t_n);        x <- u + h/2 k;  acc <- u + h/6 k;  Y <- u
+//   stage 2: k = A x   + f(t_n + h/2);  x <- u + h/2 k;  acc += h/3 k
+//   stage 3: k = A x   + f(t_n + h/2);  x <- u + h k;    acc += h/3 k
+//   stage 4: k = A x   + f(t_n + h);    u <- acc + h/6 k
+// which is algebraically the 4-stage update u + h/6 (k1 + 2k2 + 2k3 + k4).
+// Stencil neighbours come through the L1/L2 caches; every stage streams
+// the state-sized arrays once (coalesced along x).
+//
+// Adjoint operators are the exact transposes of the discrete stencils
+// (discrete adjoint with identity metric): for the 2-D system the advection
+// velocity U(y) is constant along x, so the transpose flips its sign; for the
+// 3-D system the transposed advection uses the neighbour's velocity,
+//   (A^T x)_p = (U_{p+1} x_{p+1} - U_{p-1} x_{p-1}) / (2 dx),
+// and the coupling -(u . grad)U (into component x only) becomes
+// -dU/dx_c * x_x into every component c.
+#include <cmath>
+#include <vector>
+
+#include "rsv_ops.h"
+
+namespace rsv {
+
+namespace {
+
+struct StGeom {
+  int nx, ny, nz;         // nz = 1 for 2-D
+  int64_t n;              // points per vector (x 3 components in 3-D)
+  int kg;
+  double dx, dy, dz, visc;
+  const void* f0;         // ADR2D: U(y), r(y) [ny]; ADV3D: U, dU/dx, dU/dy, dU/dz [ncell]
+  const void* f1;
+  const void* f2;
+  const void* f3;
+  int sponge_cells;
+  double sponge_amp;
+  bool adjoint;
+};
+
+template <typename R>
+__device__ __forceinline__ R sponge(int i, int j, const StGeom& g) {
+  int d = min(min(i, g.nx - 1 - i), min(j, g.ny - 1 - j));
+  if (d >= g.sponge_cells) return R(0);
+  const R s = R(g.sponge_cells);
+  const R t = (s - R(d)) / s;
+  return R(g.sponge_amp) * t * t;
+}
+
+// (A x) at cell (i, j) of one vector's 2-D field xv.
+template <typename R>
+__device__ __forceinline__ R adr2d_apply(const R* __restrict__ xv, int i, int j, const StGeom& g) {
+  const R* U = reinterpret_cast<const R*>(g.f0);
+  const R* rr = reinterpret_cast<const R*>(g.f1);
+  const int nx = g.nx, ny = g.ny;
+  const R c = xv[(int64_t)j * nx + i];
+  const R w = i > 0 ? xv[(int64_t)j * nx + i - 1] : R(0);
+  const R e = i < nx - 1 ? xv[(int64_t)j * nx + i + 1] : R(0);
+  const R s = j > 0 ? xv[(int64_t)(j - 1) * nx + i] : R(0);
+  const R nn = j < ny - 1 ? xv[(int64_t)(j + 1) * nx + i] : R(0);
+  const R ux = g.adjoint ? -U[j] : U[j];
+  const R idx2 = R(1) / (R(g.dx) * R(g.dx)), idy2 = R(1) / (R(g.dy) * R(g.dy)), i2dx = R(0.5) / R(g.dx);
+  const R nu = R(g.visc);
+  R k = (ux * i2dx + nu * idx2) * w + (-ux * i2dx + nu * idx2) * e + nu * idy2 * (s + nn);
+  k += (R(-2) * nu * (idx2 + idy2) + rr[j] - sponge<R>(i, j, g)) * c;
+  return k;
+}
+
+// (A x)_c for c = 0, 1, 2 at cell q of one vector (components at offsets c * ncell).
+template <typename R>
+__device__ __forceinline__ void adv3d_apply(const R* __restrict__ xv, int i, int j, int kz, const StGeom& g, R out[3]) {
+  const R* U = reinterpret_cast<const R*>(g.f0);
+  const R* Ux = reinterpret_cast<const R*>(g.f1);
+  const R* Uy = reinterpret_cast<const R*>(g.f2);
+  const R* Uz = reinterpret_cast<const R*>(g.f3);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int64_t ncell = (int64_t)nx * ny * nz;
+  const int64_t q = ((int64_t)kz * ny + j) * nx + i;
+  const R idx2 = R(1) / (R(g.dx) * R(g.dx)), idy2 = R(1) / (R(g.dy) * R(g.dy)), idz2 = R(1) / (R(g.dz) * R(g.dz));
+  const R i2dx = R(0.5) / R(g.dx);
+  const R nu = R(g.visc);
+  const R Uc = U[q];
+  const R Uw = i > 0 ? U[q - 1] : R(0), Ue = i < nx - 1 ? U[q + 1] : R(0);
+  R xc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R* x = xv + c * ncell;
+    const R cc = x[q];
+    const R w = i > 0 ? x[q - 1] : R(0);
+    const R e = i < nx - 1 ? x[q + 1] : R(0);
+    const R s = j > 0 ? x[q - nx] : R(0);
+    const R nn = j < ny - 1 ? x[q + nx] : R(0);
+    const R b = kz > 0 ? x[q - (int64_t)nx * ny] : R(0);
+    const R t = kz < nz - 1 ? x[q + (int64_t)nx * ny] : R(0);
+    xc[c] = cc;
+    R adv;
+    if (g.adjoint)
+      adv = (Ue * e - Uw * w) * i2dx;
+    else
+      adv = -Uc * (e - w) * i2dx;
+    out[c] = adv + nu * (idx2 * (w + e - R(2) * cc) + idy2 * (s + nn - R(2) * cc) + idz2 * (b + t - R(2) * cc));
+  }
+  if (g.adjoint) {
+    out[0] -= Ux[q] * xc[0];
+    out[1] -= Uy[q] * xc[0];
+    out[2] -= Uz[q] * xc[0];
+  } else {
+    out[0] -= Ux[q] * xc[0] + Uy[q] * xc[1] + Uz[q] * xc[2];
+  }
+}
+
+// Stage update at one state value given k (without forcing) and the forcing value.
+template <typename R, int STAGE>
+__device__ __forceinline__ void stage_update(int64_t p, R k, const R* __restrict__ u, R* __restrict__ acc,
+                                             R* __restrict__ xout, R* __restrict__ ysnap, R h) {
+  if (STAGE == 1) {
+    const R uu = u[p];
+    if (ysnap) ysnap[p] = uu;
+    xout[p] = uu + R(0.5) * h * k;
+    acc[p] = uu + (h / R(6)) * k;
+  } else if (STAGE == 2) {
+    xout[p] = u[p] + R(0.5) * h * k;
+    acc[p] += (h / R(3)) * k;
+  } else if (STAGE == 3) {
+    xout[p] = u[p] + h * k;
+    acc[p] += (h / R(3)) * k;
+  } else {
+    xout[p] = acc[p] + (h / R(6)) * k;  // xout is the state u here
+  }
+}
+
+template <typename R, int STAGE>
+__global__ void __launch_bounds__(256) adr2d_stage_kernel(StGeom g, const R* __restrict__ xin, const R* __restrict__ u,
+                                                          R* __restrict__ acc, const R* __restrict__ f, R* xout,
+                                                          R* __restrict__ ysnap, R h) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  const int v = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const int64_t base = (int64_t)v * g.n;
+  const int64_t p = base + (int64_t)j * g.nx + i;
+  R k = adr2d_apply<R>(xin + base, i, j, g);
+  if (f) k += f[p];
+  stage_update<R, STAGE>(p, k, u, acc, xout, ysnap, h);
+}
+
+template <typename R, int STAGE>
+__global__ void __launch_bounds__(256) adv3d_stage_kernel(StGeom g, const R* __restrict__ xin, const R* __restrict__ u,
+                                                          R* __restrict__ acc, const R* __restrict__ f, R* xout,
+                                                          R* __restrict__ ysnap, R h) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int jz = blockIdx.y * 8 + threadIdx.y;  // (j, kz) flattened
+  const int v = blockIdx.z;
+  if (i >= g.nx || jz >= g.ny * g.nz) return;
+  const int j = jz % g.ny, kz = jz / g.ny;
+  const int64_t base = (int64_t)v * g.n;
+  const int64_t ncell = (int64_t)g.nx * g.ny * g.nz;
+  R k[3];
+  adv3d_apply<R>(xin + base, i, j, kz, g, k);
+  const int64_t q = ((int64_t)kz * g.ny + j) * g.nx + i;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int64_t p = base + c * ncell + q;
+    R kc = k[c];
+    if (f) kc += f[p];
+    stage_update<R, STAGE>(p, kc, u, acc, xout, ysnap, h);
+  }
+}
+
+template <typename R>
+__global__ void adr2d_apply_real_kernel(StGeom g, const R* __restrict__ x, R* __restrict__ y) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  const int v = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const int64_t base = (int64_t)v * g.n;
+  y[base + (int64_t)j * g.nx + i] = adr2d_apply<R>(x + base, i, j, g);
+}
+
+// real <-> complex helpers for the operator test entry point
+template <typename R>
+__global__ void split_kernel(const cpx<R>* __restrict__ x, int64_t count, R* __restrict__ re, R* __restrict__ im) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  re[e] = x[e].re;
+  im[e] = x[e].im;
+}
+template <typename R>
+__global__ void join_kernel(const R* __restrict__ re, const R* __restrict__ im, int64_t count, cpx<R>* __restrict__ y) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  y[e] = mk<R>(re[e], im[e]);
+}
+template <typename R>
+__global__ void adv3d_apply_real_kernel(StGeom g, const R* __restrict__ x, R* __restrict__ y) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int jz = blockIdx.y * 8 + threadIdx.y;
+  const int v = blockIdx.z;
+  if (i >= g.nx || jz >= g.ny * g.nz) return;
+  const int j = jz % g.ny, kz = jz / g.ny;
+  const int64_t base = (int64_t)v * g.n;
+  const int64_t ncell = (int64_t)g.nx * g.ny * g.nz;
+  R k[3];
+  adv3d_apply<R>(x + base, i, j, kz, g, k);
+  const int64_t q = ((int64_t)kz * g.ny + j) * g.nx + i;
+  for (int c = 0; c < 3; ++c) y[base + c * ncell + q] = k[c];
+}
+
+template <typename R>
+rsv_status upload_real(rsv_operator op, const std::vector<double>& v, void** dst) {
+  std::vector<R> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (R)v[i];
+  return upload(op, o.data(), o.size() * sizeof(R), dst);
+}
+
+rsv_status upload_fields(rsv_operator op, const std::vector<std::vector<double>>& fields) {
+  for (size_t a = 0; a < fields.size(); ++a) {
+    rsv_status s = op->prec == RSV_PREC_FP64 ? upload_real<double>(op, fields[a], &op->fld[a])
+                                             : upload_real<float>(op, fields[a], &op->fld[a]);
+    if (s != RSV_OK) return s;
+  }
+  return RSV_OK;
+}
+
+StGeom geom_of(rsv_operator op, int kg, bool adjoint) {
+  StGeom g;
+  g.nx = op->nx;
+  g.ny = op->ny;
+  g.nz = op->kind == RSV_OP_ADV3D ? op->nz : 1;
+  g.n = op->n;
+  g.kg = kg;
+  g.dx = op->c_dx;
+  g.dy = op->c_dy;
+  g.dz = op->c_dz;
+  g.visc = op->visc;
+  g.f0 = op->fld[0];
+  g.f1 = op->fld[1];
+  g.f2 = op->fld[2];
+  g.f3 = op->fld[3];
+  g.sponge_cells = op->sponge_cells;
+  g.sponge_amp = op->sponge_amp;
+  g.adjoint = adjoint;
+  return g;
+}
+
+template <typename R, int STAGE>
+cudaError_t launch_stage(rsv_operator op, const StGeom& g, const R* xin, const R* u, R* acc, const R* f, R* xout,
+                         R* ysnap, R h) {
+  if (op->kind == RSV_OP_ADR2D) {
+    dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 7) / 8), (unsigned)g.kg);
+    adr2d_stage_kernel<R, STAGE><<<grid, dim3(32, 8), 0, op->stream>>>(g, xin, u, acc, f, xout, ysnap, h);
+  } else {
+    dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny * g.nz + 7) / 8), (unsigned)g.kg);
+    adv3d_stage_kernel<R, STAGE><<<grid, dim3(32, 8), 0, op->stream>>>(g, xin, u, acc, f, xout, ysnap, h);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// 2-D jet: U(y) = 0.5 (1 + tanh((0.5 - |y|)/delta)), r(y) = -kappa dU/dy, sponge on the fly.
+rsv_status build_adr2d(rsv_operator op, const rsv_operator_desc* d) {
+  if (d->nx < 3 || d->ny < 3 || !(d->lx > 0) || !(d->ly > 0) || !(d->jet_delta > 0))
+    return fail(RSV_ERR_INVALID_ARG, "ADR2D needs nx, ny >= 3 and positive lengths");
+  op->nx = d->nx;
+  op->ny = d->ny;
+  op->nz = 1;
+  op->n = (int64_t)d->nx * d->ny;
+  op->n_inst = 1;
+  op->inst_off.assign(1, 0);
+  op->inst_len.assign(1, op->n);
+  op->real_state = true;
+  op->c_dx = d->lx / (d->nx + 1);
+  op->c_dy = d->ly / (d->ny + 1);
+  op->visc = d->visc;
+  op->sponge_cells = d->sponge_cells;
+  op->sponge_amp = d->sponge_amp;
+  std::vector<double> U(d->ny), r(d->ny);
+  for (int j = 0; j < d->ny; ++j) {
+    const double y = -0.5 * d->ly + (j + 1) * op->c_dy;
+    const double arg = (0.5 - std::fabs(y)) / d->jet_delta;
+    U[j] = 0.5 * (1.0 + std::tanh(arg));
+    const double sg = (y > 0) - (y < 0);
+    const double ch = std::cosh(arg);
+    r[j] = -d->kappa * (0.5 / (ch * ch) * (-sg / d->jet_delta));
+  }
+  return upload_fields(op, {U, r});
+}
+
+// 3-D boundary layer: U = erf(r / delta(x)) and its exact gradient (0 on the axis r = 0).
+rsv_status build_adv3d(rsv_operator op, const rsv_operator_desc* d) {
+  if (d->nx < 3 || d->ny < 3 || d->nz < 3 || !(d->lx > 0) || !(d->ly > 0) || !(d->lz > 0))
+    return fail(RSV_ERR_INVALID_ARG, "ADV3D needs nx, ny, nz >= 3 and positive lengths");
+  op->nx = d->nx;
+  op->ny = d->ny;
+  op->nz = d->nz;
+  const int64_t ncell = (int64_t)d->nx * d->ny * d->nz;
+  op->n = 3 * ncell;
+  op->n_inst = 1;
+  op->inst_off.assign(1, 0);
+  op->inst_len.assign(1, op->n);
+  op->real_state = true;
+  op->c_dx = d->lx / (d->nx + 1);
+  op->c_dy = d->ly / (d->ny + 1);
+  op->c_dz = d->lz / (d->nz + 1);
+  op->visc = d->visc;
+  std::vector<double> U(ncell), Ux(ncell), Uy(ncell), Uz(ncell);
+  const double dd = (d->delta1 - d->delta0) / d->lx;
+  for (int kz = 0; kz < d->nz; ++kz)
+    for (int j = 0; j < d->ny; ++j)
+      for (int i = 0; i < d->nx; ++i) {
+        const int64_t q = ((int64_t)kz * d->ny + j) * d->nx + i;
+        const double x = (i + 1) * op->c_dx;
+        const double y = -0.5 * d->ly + (j + 1) * op->c_dy;
+        const double z = -0.5 * d->lz + (kz + 1) * op->c_dz;
+        const double del = d->delta0 + dd * x;
+        const double r = std::sqrt(y * y + z * z);
+        const double gg = 2.0 / std::sqrt(M_PI) * std::exp(-(r / del) * (r / del));
+        U[q] = std::erf(r / del);
+        Ux[q] = gg * (-r * dd / (del * del));
+        Uy[q] = r > 0 ? gg * (y / (r * del)) : 0.0;
+        Uz[q] = r > 0 ? gg * (z / (r * del)) : 0.0;
+      }
+  return upload_fields(op, {U, Ux, Uy, Uz});
+}
+
+// Workspace behind the state in the march: two stage-input buffers and the accumulator.
+size_t stencil_scratch_bytes(rsv_operator op, int kg) {
+  return 3 * (size_t)kg * op->n * (op->prec == RSV_PREC_FP64 ? 8 : 4);
+}
+
+template <typename R>
+cudaError_t stencil_march_tile(rsv_operator op, const MarchTile& t, void* state, const void* F, void* Y) {
+  const StGeom g = geom_of(op, t.kg, t.adjoint);
+  const int64_t rows = (int64_t)t.kg * op->n;
+  R* u = static_cast<R*>(state);
+  R* xa = u + rows;
+  R* xb = xa + rows;
+  R* acc = xb + rows;
+  const R h = (R)op->h;
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < t.steps && e == cudaSuccess; ++s) {
+    const int64_t n = t.n0 + s;
+    const bool forced = F != nullptr && n < t.n_forced;
+    const R* Fr = static_cast<const R*>(F);
+    const R* f0 = forced ? Fr + (size_t)(2 * s) * rows : nullptr;
+    const R* fh = forced ? Fr + (size_t)(2 * s + 1) * rows : nullptr;
+    const R* f1 = forced ? Fr + (size_t)(2 * s + 2) * rows : nullptr;
+    R* ys = (Y != nullptr && s >= t.y_first) ? static_cast<R*>(Y) + (size_t)s * rows : nullptr;
+    // stage inputs ping-pong between xa and xb: a stage never writes the array its stencil reads
+    e = launch_stage<R, 1>(op, g, u, u, acc, f0, xa, ys, h);
+    if (e == cudaSuccess) e = launch_stage<R, 2>(op, g, xa, u, acc, fh, xb, nullptr, h);
+    if (e == cudaSuccess) e = launch_stage<R, 3>(op, g, xb, u, acc, fh, xa, nullptr, h);
+    if (e == cudaSuccess) e = launch_stage<R, 4>(op, g, xa, nullptr, acc, f1, u, nullptr, h);
+  }
+  if (e == cudaSuccess) e = check_finite(op, u, rows, true);
+  return e;
+}
+
+template <typename R>
+cudaError_t stencil_apply(rsv_operator op, const void* x, int k, bool adjoint, void* y) {
+  // complex blocks: the real operator acts on real and imaginary parts alike (test entry point)
+  const StGeom g = geom_of(op, k, adjoint);
+  const int64_t count = (int64_t)k * op->n;
+  R* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&tmp, 4 * count * sizeof(R), op->stream);
+  if (e != cudaSuccess) return e;
+  const unsigned b = (unsigned)((count + 255) / 256);
+  split_kernel<R><<<b, 256, 0, op->stream>>>((const cpx<R>*)x, count, tmp, tmp + count);
+  for (int part = 0; part < 2; ++part) {
+    if (op->kind == RSV_OP_ADR2D) {
+      dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 7) / 8), (unsigned)k);
+      adr2d_apply_real_kernel<R><<<grid, dim3(32, 8), 0, op->stream>>>(g, tmp + part * count, tmp + (2 + part) * count);
+    } else {
+      dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny * g.nz + 7) / 8), (unsigned)k);
+      adv3d_apply_real_kernel<R><<<grid, dim3(32, 8), 0, op->stream>>>(g, tmp + part * count, tmp + (2 + part) * count);
+    }
+  }
+  join_kernel<R><<<b, 256, 0, op->stream>>>(tmp + 2 * count, tmp + 3 * count, count, (cpx<R>*)y);
+  e = cudaGetLastError();
+  cudaFreeAsync(tmp, op->stream);
+  return e;
+}
+
+template cudaError_t stencil_march_tile<double>(rsv_operator, const MarchTile&, void*, const void*, void*);
+template cudaError_t stencil_march_tile<float>(rsv_operator, const MarchTile&, void*, const void*, void*);
+template cudaError_t stencil_apply<double>(rsv_operator, const void*, int, bool, void*);
+template cudaError_t stencil_apply<float>(rsv_operator, const void*, int, bool, void*);
+
+}  // namespace rsv
