@@ -317,7 +317,7 @@ def run_ours(args):
 
     # accuracy: the timed path's gains against the FP64 path (itself parity-tested against the oracle)
     acc = None
-    if prec_name != "fp64" and not args.skip_accuracy and dense is None:
+    if prec_name != "fp64" and not args.skip_accuracy and dense is None and w.n * w.k * w.n_omega < 2 ** 27:
         op64 = rsv.create_for_workload(w, rsv.RSV_PREC_FP64, stream=stream.cuda_stream, dense_matrix=dense)
         g64 = np.zeros_like(gains)
         rsv.rsv_gains_modes(op64, omega_dev.to(torch.complex128), w.k, w.n_power_iter, w.n_modes, g64, **opts)
@@ -329,7 +329,7 @@ def run_ours(args):
 
     dom = max(prof, key=lambda c: prof[c][1])
     rows = w.k * w.n
-    tile = args.tile or 256
+    tile = args.tile or (64 if w.real_state else 256)
     roof = kernel_model(dom, w, prec_name, tile, prof[dom][0], prof[dom][1], rows)
     launches = sum(v[0] for v in prof.values())
     steps_per_march = {"ssrm": (w.n_transient_windows + 1) * n_t, "trm": n_t + w.tail_steps}[w.variant]

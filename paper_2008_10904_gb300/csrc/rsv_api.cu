@@ -373,10 +373,35 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
   Schedule sc;
   rsv_status st = make_schedule(op, opts, &sc);
   if (st != RSV_OK) return st;
-  const int S = (opts && opts->tile_steps > 0) ? opts->tile_steps : default_tile_steps(op);
-  const int kg = march_group_size(op, k, S);
   const int64_t n = op->n;
   const size_t se = state_elem_bytes(op);
+  // Tile length S and vector-group size kg: the requested / default tile, shrunk (S down to 16,
+  // then kg halved) until the march workspace fits in 90% of the device memory not held by others.
+  int S = (opts && opts->tile_steps > 0) ? opts->tile_steps : default_tile_steps(op);
+  int kg = k;
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = (size_t)1 << 62;
+    }
+    const size_t held = op->ws_state.bytes + op->ws_ftile.bytes + op->ws_ysnap.bytes + op->ws_acc.bytes +
+                        op->ws_coef.bytes + op->ws_coef2.bytes;
+    const double budget = 0.9 * (double)(free_b + held);
+    auto need = [&](int s_, int kg_) {
+      const double rows_ = (double)kg_ * n;
+      double b = rows_ * se + (double)stage_scratch_bytes(op, kg_) + (2.0 * s_ + 1) * rows_ * se + s_ * rows_ * se;
+      if (op->prec != RSV_PREC_FP64) b += (double)op->n_omega * rows_ * sizeof(cpx<double>);
+      if (op->kind == RSV_OP_DENSE) b += 2.0 * op->n_omega * rows_ * 2 * sizeof(R);
+      return b;
+    };
+    while (need(S, kg) > budget && (S > 16 || kg > 1)) {
+      if (S > 16)
+        S = std::max(16, S / 2);
+      else
+        kg = (kg + 1) / 2;
+    }
+  }
   const cudaStream_t stream = op->stream;
   cudaError_t e;
   const int64_t rows_max = (int64_t)kg * n;

@@ -21,7 +21,6 @@ rsv_status build_adv3d(rsv_operator op, const rsv_operator_desc* d);
 rsv_status upload(rsv_operator op, const void* host, size_t bytes, void** dst);
 
 int default_tile_steps(rsv_operator op);
-int march_group_size(rsv_operator op, int k, int S);
 size_t stage_scratch_bytes(rsv_operator op, int kg);
 
 // S RK4 steps of the operator's stage kernel(s) on the state block (kg vectors).
