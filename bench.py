@@ -329,7 +329,7 @@ def run_ours(args):
 
     dom = max(prof, key=lambda c: prof[c][1])
     rows = w.k * w.n
-    tile = args.tile or (64 if w.real_state else 256)
+    tile = args.tile or 256
     roof = kernel_model(dom, w, prec_name, tile, prof[dom][0], prof[dom][1], rows)
     launches = sum(v[0] for v in prof.values())
     steps_per_march = {"ssrm": (w.n_transient_windows + 1) * n_t, "trm": n_t + w.tail_steps}[w.variant]

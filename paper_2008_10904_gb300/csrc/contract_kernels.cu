@@ -9,8 +9,8 @@
 //   acc[j][r] += sum_s Y[s][r] exp(-i sgn w_j t_s),  t_s = (n0 + s) h.
 //
 // Both are contractions over a short dimension (frequencies or tile steps)
-// that stream one long dimension r (state rows): each thread owns one row and
-// keeps a chunk of outputs in registers; the exact twiddles exp(i pi q / 2N_T)
+// that stream one long dimension r (state rows): each thread owns a few rows
+// and keeps a chunk of outputs in registers; the exact twiddles exp(i pi q / 2N_T)
 // (integer phase index q) are staged in shared memory per block.  Products
 // and in-tile sums run in the element precision R; in-tile partial sums are
 // folded into FP64 registers every 64 steps and then added to the FP64
@@ -25,47 +25,76 @@ constexpr int kTauChunk = 8;
 constexpr int kOmChunk = 8;
 constexpr int kSChunk = 64;
 
+// Register blocking: each thread owns RB rows (RB = 4 in FP32, 2 in FP64) and a
+// chunk of 8 output columns (synthesis: stage times, analysis: frequencies), so
+// every twiddle read from shared memory feeds RB complex multiply-adds.
+template <typename R>
+struct Blk {
+  static constexpr int RB = sizeof(R) == 4 ? 4 : 2;
+};
+
 template <typename R, bool REAL>
 __global__ void __launch_bounds__(kTPB) synth_kernel(TileGeom g, const cpx<R>* __restrict__ fhat,
                                                      const cpx<R>* __restrict__ tw,
                                                      const int64_t* __restrict__ pj,
                                                      const float* __restrict__ cw, void* __restrict__ Fout) {
+  constexpr int RB = Blk<R>::RB;
   extern __shared__ unsigned char smem_raw[];
-  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);  // [kTauChunk][n_omega]
+  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);  // [n_omega][kTauChunk]
   const int n_tau = g.n_tau > 0 ? g.n_tau : 2 * g.steps + 1;
-  const int tau0 = blockIdx.y * kTauChunk;
+  // blocks of the same rows are adjacent in launch order (chunk index fastest), so the
+  // coefficient rows they all read stay in L2
+  const int n_chunks = (n_tau + kTauChunk - 1) / kTauChunk;
+  const int tau0 = (int)(blockIdx.x % n_chunks) * kTauChunk;
+  const int64_t row_block = blockIdx.x / n_chunks;
   const int nt = min(kTauChunk, n_tau - tau0);
-  for (int e = threadIdx.x; e < nt * g.n_omega; e += blockDim.x) {
-    const int t = e / g.n_omega, j = e - t * g.n_omega;
-    const int64_t q = phase_index(g.sgn * pj[j], 2 * g.n0 + (int64_t)(tau0 + t) * g.tau_stride, g.m4);
-    cpx<R> v = tw[q];
-    if (REAL) v = R(cw[j]) * v;
-    stw[t * g.n_omega + j] = v;
+  for (int e = threadIdx.x; e < kTauChunk * g.n_omega; e += blockDim.x) {
+    const int j = e / kTauChunk, t = e - j * kTauChunk;
+    cpx<R> v = mk<R>(0, 0);
+    if (t < nt) {
+      const int64_t q = phase_index(g.sgn * pj[j], 2 * g.n0 + (int64_t)(tau0 + t) * g.tau_stride, g.m4);
+      v = tw[q];
+      if (REAL) v = R(cw[j]) * v;
+    }
+    stw[j * kTauChunk + t] = v;
   }
   __syncthreads();
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= g.rows) return;
-  cpx<R> acc[kTauChunk];
+  const int64_t r0 = row_block * (kTPB * RB) + threadIdx.x;
+  bool ok[RB];
 #pragma unroll
-  for (int t = 0; t < kTauChunk; ++t) acc[t] = mk<R>(0, 0);
+  for (int b = 0; b < RB; ++b) ok[b] = r0 + b * kTPB < g.rows;
+  cpx<R> acc[RB][kTauChunk];
+#pragma unroll
+  for (int b = 0; b < RB; ++b)
+#pragma unroll
+    for (int t = 0; t < kTauChunk; ++t) acc[b][t] = mk<R>(0, 0);
   for (int j = 0; j < g.n_omega; ++j) {
-    const cpx<R> x = fhat[(int64_t)j * g.coef_stride + r];
+    cpx<R> x[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) x[b] = ok[b] ? fhat[(int64_t)j * g.coef_stride + r0 + b * kTPB] : mk<R>(0, 0);
 #pragma unroll
     for (int t = 0; t < kTauChunk; ++t) {
-      const cpx<R> w = stw[t * g.n_omega + j];
-      if (REAL) {
-        acc[t].re = fma(w.re, x.re, fma(-w.im, x.im, acc[t].re));
-      } else {
-        cfma(acc[t], w, x);
+      const cpx<R> w = stw[j * kTauChunk + t];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        if (REAL)
+          acc[b][t].re = fma(w.re, x[b].re, fma(-w.im, x[b].im, acc[b][t].re));
+        else
+          cfma(acc[b][t], w, x[b]);
       }
     }
   }
-  if (REAL) {
-    R* F = reinterpret_cast<R*>(Fout);
-    for (int t = 0; t < nt; ++t) F[(int64_t)(tau0 + t) * g.rows + r] = acc[t].re;
-  } else {
-    cpx<R>* F = reinterpret_cast<cpx<R>*>(Fout);
-    for (int t = 0; t < nt; ++t) F[(int64_t)(tau0 + t) * g.rows + r] = acc[t];
+#pragma unroll
+  for (int b = 0; b < RB; ++b) {
+    if (!ok[b]) continue;
+    const int64_t r = r0 + b * kTPB;
+    if (REAL) {
+      R* F = reinterpret_cast<R*>(Fout);
+      for (int t = 0; t < nt; ++t) F[(int64_t)(tau0 + t) * g.rows + r] = acc[b][t].re;
+    } else {
+      cpx<R>* F = reinterpret_cast<cpx<R>*>(Fout);
+      for (int t = 0; t < nt; ++t) F[(int64_t)(tau0 + t) * g.rows + r] = acc[b][t];
+    }
   }
 }
 
@@ -74,13 +103,22 @@ __global__ void __launch_bounds__(kTPB) analysis_kernel(TileGeom g, const void* 
                                                         const cpx<R>* __restrict__ tw,
                                                         const int64_t* __restrict__ pj,
                                                         cpx<double>* __restrict__ acc, int64_t acc_stride) {
+  constexpr int RB = 2;
   __shared__ cpx<R> stw[kSChunk][kOmChunk];
-  const int j0 = blockIdx.y * kOmChunk;
+  // frequency chunk fastest in launch order: the blocks sharing a row block reuse its snapshots in L2
+  const int n_chunks = (g.n_omega + kOmChunk - 1) / kOmChunk;
+  const int j0 = (int)(blockIdx.x % n_chunks) * kOmChunk;
+  const int64_t row_block = blockIdx.x / n_chunks;
   const int nj = min(kOmChunk, g.n_omega - j0);
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  cpx<double> a64[kOmChunk];
+  const int64_t r0 = row_block * (kTPB * RB) + threadIdx.x;
+  bool ok[RB];
 #pragma unroll
-  for (int jj = 0; jj < kOmChunk; ++jj) a64[jj] = mk<double>(0, 0);
+  for (int b = 0; b < RB; ++b) ok[b] = r0 + b * kTPB < g.rows;
+  cpx<double> a64[RB][kOmChunk];
+#pragma unroll
+  for (int b = 0; b < RB; ++b)
+#pragma unroll
+    for (int jj = 0; jj < kOmChunk; ++jj) a64[b][jj] = mk<double>(0, 0);
   for (int sc = s0; sc < s1; sc += kSChunk) {
     const int ns = min(kSChunk, s1 - sc);
     __syncthreads();
@@ -91,34 +129,56 @@ __global__ void __launch_bounds__(kTPB) analysis_kernel(TileGeom g, const void* 
       stw[s][jj] = v;
     }
     __syncthreads();
-    if (r < g.rows) {
-      cpx<R> a[kOmChunk];
+    cpx<R> a[RB][kOmChunk];
 #pragma unroll
-      for (int jj = 0; jj < kOmChunk; ++jj) a[jj] = mk<R>(0, 0);
-      for (int s = 0; s < ns; ++s) {
-        cpx<R> y;
-        if (REAL) {
-          y = mk<R>(reinterpret_cast<const R*>(Yin)[(int64_t)(sc + s) * g.rows + r], R(0));
-        } else {
-          y = reinterpret_cast<const cpx<R>*>(Yin)[(int64_t)(sc + s) * g.rows + r];
-        }
+    for (int b = 0; b < RB; ++b)
 #pragma unroll
-        for (int jj = 0; jj < kOmChunk; ++jj) cfma_conj(a[jj], stw[s][jj], y);
+      for (int jj = 0; jj < kOmChunk; ++jj) a[b][jj] = mk<R>(0, 0);
+    for (int s = 0; s < ns; ++s) {
+      cpx<R> y[RB];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int64_t off = (int64_t)(sc + s) * g.rows + r0 + b * kTPB;
+        if (!ok[b])
+          y[b] = mk<R>(0, 0);
+        else if (REAL)
+          y[b] = mk<R>(reinterpret_cast<const R*>(Yin)[off], R(0));
+        else
+          y[b] = reinterpret_cast<const cpx<R>*>(Yin)[off];
       }
 #pragma unroll
       for (int jj = 0; jj < kOmChunk; ++jj) {
-        a64[jj].re += (double)a[jj].re;
-        a64[jj].im += (double)a[jj].im;
+        const cpx<R> w = stw[s][jj];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+          if (REAL) {
+            a[b][jj].re = fma(w.re, y[b].re, a[b][jj].re);
+            a[b][jj].im = fma(-w.im, y[b].re, a[b][jj].im);
+          } else {
+            cfma_conj(a[b][jj], w, y[b]);
+          }
+        }
       }
     }
+#pragma unroll
+    for (int b = 0; b < RB; ++b)
+#pragma unroll
+      for (int jj = 0; jj < kOmChunk; ++jj) {
+        a64[b][jj].re += (double)a[b][jj].re;
+        a64[b][jj].im += (double)a[b][jj].im;
+      }
   }
-  if (r >= g.rows) return;
-  for (int jj = 0; jj < nj; ++jj) {
-    cpx<double>* p = acc + (int64_t)(j0 + jj) * acc_stride + r;
-    cpx<double> v = *p;
-    v.re += a64[jj].re;
-    v.im += a64[jj].im;
-    *p = v;
+#pragma unroll
+  for (int b = 0; b < RB; ++b) {
+    if (!ok[b]) continue;
+    const int64_t r = r0 + b * kTPB;
+    for (int jj = 0; jj < nj; ++jj) {
+      cpx<double>* p = acc + (int64_t)(j0 + jj) * acc_stride + r;
+      cpx<double> v = *p;
+      v.re += a64[b][jj].re;
+      v.im += a64[b][jj].im;
+      *p = v;
+    }
   }
 }
 
@@ -138,7 +198,9 @@ template <typename R>
 cudaError_t launch_synth(const TileGeom& g, const void* fhat, const void* tw, const int64_t* pj, const float* cw,
                          bool real_state, void* F, cudaStream_t st) {
   const int n_tau = g.n_tau > 0 ? g.n_tau : 2 * g.steps + 1;
-  dim3 grid((unsigned)((g.rows + kTPB - 1) / kTPB), (unsigned)((n_tau + kTauChunk - 1) / kTauChunk));
+  const int64_t per_block = (int64_t)kTPB * Blk<R>::RB;
+  const int64_t blocks = ((g.rows + per_block - 1) / per_block) * ((n_tau + kTauChunk - 1) / kTauChunk);
+  dim3 grid((unsigned)blocks);
   const size_t smem = sizeof(cpx<R>) * kTauChunk * g.n_omega;
   if (real_state) {
     if (smem > 48 * 1024)
@@ -156,7 +218,8 @@ template <typename R>
 cudaError_t launch_analysis(const TileGeom& g, const void* Y, int s0, int s1, const void* tw, const int64_t* pj,
                             bool real_state, cpx<double>* acc, int64_t acc_stride, cudaStream_t st) {
   if (s1 <= s0) return cudaSuccess;
-  dim3 grid((unsigned)((g.rows + kTPB - 1) / kTPB), (unsigned)((g.n_omega + kOmChunk - 1) / kOmChunk));
+  const int64_t blocks = ((g.rows + 2 * kTPB - 1) / (2 * kTPB)) * ((g.n_omega + kOmChunk - 1) / kOmChunk);
+  dim3 grid((unsigned)blocks);
   if (real_state)
     analysis_kernel<R, true><<<grid, kTPB, 0, st>>>(g, Y, s0, s1, (const cpx<R>*)tw, pj, acc, acc_stride);
   else

@@ -80,9 +80,7 @@ rsv_status build_gl1d(rsv_operator op, const rsv_operator_desc* d) {
 }
 
 
-int default_tile_steps(rsv_operator op) {
-  return (op->kind == RSV_OP_ADR2D || op->kind == RSV_OP_ADV3D) ? 64 : 256;
-}
+int default_tile_steps(rsv_operator op) { return 256; }
 
 static size_t elem_size(rsv_operator op) { return op->prec == RSV_PREC_FP64 ? 8 : 4; }
 
