@@ -193,15 +193,17 @@ rsv_status rsv_gains_modes(rsv_operator op, const void* omega_block, int32_t k, 
  * act on real and imaginary parts alike).  For testing the operator kernels. */
 rsv_status rsv_apply_operator(rsv_operator op, const void* x, int32_t k, int32_t adjoint, void* y);
 
-/* Kernel-time accounting.  With enable = 1 the operator brackets every launch
- * of its device kernels with CUDA events on its stream, grouped by category:
- *   0 synthesis, 1 march (operator stages), 2 analysis, 3 glue (Gram / combine).
- * rsv_profile_read returns the launch count and the summed event time (ms) of
- * one category since the last reset (it synchronises the stream); enable = 0
- * stops recording, and rsv_profile_reset clears the totals. */
+/* Kernel-time accounting.  With enable = 1 the operator brackets each group
+ * of device launches of one kind with CUDA events on its stream, grouped by
+ * category: 0 synthesis, 1 march (operator stages of one time tile),
+ * 2 analysis, 3 glue (Gram / combine / coefficient transforms).
+ * rsv_profile_read returns, for one category since the last reset, the number
+ * of bracketed groups, the number of kernels they launched, and their summed
+ * event time in ms (it synchronises the stream).  enable = 0 stops recording;
+ * rsv_profile_reset clears the totals. */
 rsv_status rsv_profile_enable(rsv_operator op, int32_t enable);
 rsv_status rsv_profile_reset(rsv_operator op);
-rsv_status rsv_profile_read(rsv_operator op, int32_t category, int64_t* launches, double* ms);
+rsv_status rsv_profile_read(rsv_operator op, int32_t category, int64_t* groups, int64_t* kernels, double* ms);
 
 /* One-line description of the operator's execution path (kernels chosen for
  * this GPU, e.g. the dense step's tensor-core variant and cluster capacity),

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kTPB) analysis_kernel(TileGeom g, const void* 
                                                         const cpx<R>* __restrict__ tw,
                                                         const int64_t* __restrict__ pj,
                                                         cpx<double>* __restrict__ acc, int64_t acc_stride) {
-  constexpr int RB = 2;
+  constexpr int RB = REAL ? 2 : 1;  // complex state: fewer registers, more resident blocks
   __shared__ cpx<R> stw[kSChunk][kOmChunk];
   // frequency chunk fastest in launch order: the blocks sharing a row block reuse its snapshots in L2
   const int n_chunks = (g.n_omega + kOmChunk - 1) / kOmChunk;
@@ -218,7 +218,8 @@ template <typename R>
 cudaError_t launch_analysis(const TileGeom& g, const void* Y, int s0, int s1, const void* tw, const int64_t* pj,
                             bool real_state, cpx<double>* acc, int64_t acc_stride, cudaStream_t st) {
   if (s1 <= s0) return cudaSuccess;
-  const int64_t blocks = ((g.rows + 2 * kTPB - 1) / (2 * kTPB)) * ((g.n_omega + kOmChunk - 1) / kOmChunk);
+  const int rb = real_state ? 2 : 1;
+  const int64_t blocks = ((g.rows + rb * kTPB - 1) / (rb * kTPB)) * ((g.n_omega + kOmChunk - 1) / kOmChunk);
   dim3 grid((unsigned)blocks);
   if (real_state)
     analysis_kernel<R, true><<<grid, kTPB, 0, st>>>(g, Y, s0, s1, (const cpx<R>*)tw, pj, acc, acc_stride);

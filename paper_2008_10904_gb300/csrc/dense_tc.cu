@@ -179,24 +179,35 @@ __global__ void __launch_bounds__(256, 1) dense_tc_step_kernel(TcStepArgs a) {
 // Persistent variant (no clusters): one launch marches a whole time tile with
 // MB * CS CTAs, one per SM, all resident at once.  CTA (mb, j) keeps the A
 // tile of row block mb and K slice j in shared memory for the whole tile.
-// Per step it waits until row blocks 2j and 2j+1 (the producers of its K
-// slice) have published the step, bulk-copies its X slice, runs the MMAs,
-// and adds its 128 x 64 partial into the row block's FP32 accumulator with
-// vector atomics in L2.  The last CTA of the row block to arrive (arrival
-// counter) does the RK4 epilogue for the block's 64 rows, re-zeroes the
-// accumulator and publishes the block's step counter.  Every row block reads
-// all K slices, so no CTA can run more than one step ahead of any other:
-// accumulators, counters and X operands are double-buffered by step parity.
-// Spins are bounded and stop early once any CTA has set the error.
+//
+// The test vectors are split into up to four independent chains of 8
+// vectors (MMA N = 16: 8 real + 8 imaginary columns).  Each chain is driven
+// by its own four warps with its own operand buffers, mbarriers, tensor-memory
+// columns, accumulators and step counters, so while one chain waits on its
+// hand-off latency the tensor core works on another.  Per chain and step a
+// CTA waits until row blocks 2j and 2j+1 (the producers of its K slice) have
+// published the step, bulk-copies its X slice, runs the MMAs, and adds its
+// 128 x 16 partial into the row block's FP32 accumulator with vector atomics
+// in L2.  The last CTA of the row block to arrive (arrival counter) does the
+// RK4 epilogue for the block's 64 rows, re-zeroes the accumulator and
+// publishes the chain's step counter for the block.  Every row block reads
+// all K slices, so no CTA runs more than one step ahead of any other within
+// a chain: accumulators, counters and X operands are double-buffered by step
+// parity.  Spins are bounded and stop early once any CTA has set the error.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kSmemPersistent = 4 * (2 * kATileFloats + 2 * kXTileFloats) + 64;
+constexpr int kChainVec = 8;                         // vectors per chain
+constexpr int kChainN = 2 * kChainVec;               // MMA N per chain
+constexpr int kMaxChains = 4;
+constexpr uint32_t kXcFloats = kChainN * kTileK;     // 2048 floats = 8 KB per hi / lo
+constexpr uint32_t kSmemPersistent = 4 * (2 * kATileFloats + kMaxChains * 2 * kXcFloats) + 256;
 constexpr uint32_t kSpinTries = 1u << 24;
 
 struct TcMarchArgs {
   const float* A;
-  float* X;                 // [2][CS][2][kXTileFloats]
-  float* acc;               // [2][MB][kM][kN]
-  int* cnt;                 // [2][MB]
+  float* X;                 // [chains][2][CS][2][kXcFloats]
+  float* acc;               // [chains][2][MB][kM][kChainN]
+  int* cnt;                 // [chains][2][MB]
+  int* ready;               // [chains][MB]
   cpx<float>* u;            // [2][kg][n]
   const cpx<float>* F;      // [steps][kg][n] or null
   cpx<float>* Y;            // [steps][kg][n] or null
@@ -204,29 +215,31 @@ struct TcMarchArgs {
   int steps;
   int64_t n_forced;
   int y_first;
-  int n, kg, cs;
-  int* ready;               // [MB]
+  int n, kg, cs, chains;
   int* err;
 };
 
-__global__ void __launch_bounds__(256, 1) dense_tc_march_kernel(TcMarchArgs a) {
+__device__ __forceinline__ void chain_bar(int chain) {
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + chain) : "memory");
+}
+
+__global__ void __launch_bounds__(512, 1) dense_tc_march_kernel(TcMarchArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   float* A_hi = reinterpret_cast<float*>(smem);
   float* A_lo = A_hi + kATileFloats;
-  float* X_hi = A_lo + kATileFloats;
-  float* X_lo = X_hi + kXTileFloats;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(X_lo + kXTileFloats);  // [0] A, [1] X, [2] MMA
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 3);
-  int* last = reinterpret_cast<int*>(tbase + 1);
+  float* Xs = A_lo + kATileFloats;                                         // [chain][hi, lo][kXcFloats]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Xs + kMaxChains * 2 * kXcFloats);  // [0] A, then 2 per chain
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 1 + 2 * kMaxChains);
+  int* last = reinterpret_cast<int*>(tbase + 1);                          // [chain]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int chain = warp >> 2;                  // warps 4c .. 4c + 3 drive chain c
+  const int ctid = tid & 127;                   // thread index within the chain
   const int MB = a.n / kTileRows;
   const int mb = blockIdx.x / a.cs;
   const int j = blockIdx.x % a.cs;
   if (tid == 0) {
-    tc::mbar_init(&bars[0], 1);
-    tc::mbar_init(&bars[1], 1);
-    tc::mbar_init(&bars[2], 1);
+    for (int b = 0; b < 1 + 2 * kMaxChains; ++b) tc::mbar_init(&bars[b], 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tbase, 64);
@@ -241,113 +254,132 @@ __global__ void __launch_bounds__(256, 1) dense_tc_march_kernel(TcMarchArgs a) {
     tc::bulk_g2s(A_lo, at + kATileFloats, 4 * kATileFloats, &bars[0]);
   }
   bool ok = tc::mbar_wait(&bars[0], 0, kWaitTries);
-  const size_t xset = (size_t)a.cs * 2 * kXTileFloats;
-  const int64_t rows = (int64_t)a.kg * a.n;
-  const uint32_t idesc = tc::idesc_tf32(kM, kN);
-  const uint32_t sbo = (kTileK / 4) * 128;
-  volatile int* errv = a.err;
-
-  for (int s = 0; s < a.steps; ++s) {
-    const int64_t n = a.n0 + s;
-    const int par = (int)(n & 1);
-    if (tid == 0) {
-      bool got = false;
-      for (uint32_t it = 0; it < kSpinTries; ++it) {
-        if (*errv != 0) break;
-        if (tc::ld_acquire(&a.ready[2 * j]) >= (int)n && tc::ld_acquire(&a.ready[2 * j + 1]) >= (int)n) {
-          got = true;
-          break;
+  __syncthreads();
+  if (chain < a.chains) {
+    float* X_hi = Xs + (size_t)chain * 2 * kXcFloats;
+    float* X_lo = X_hi + kXcFloats;
+    uint64_t* bar_x = &bars[1 + 2 * chain];
+    uint64_t* bar_m = &bars[2 + 2 * chain];
+    const uint32_t tcol = tmem + (uint32_t)(chain * kChainN);
+    const size_t xset = (size_t)a.cs * 2 * kXcFloats;
+    float* Xg = a.X + (size_t)chain * 2 * xset;
+    float* accg = a.acc + (size_t)chain * 2 * MB * kM * kChainN;
+    int* cnt = a.cnt + chain * 2 * MB;
+    int* ready = a.ready + chain * MB;
+    const int64_t rows = (int64_t)a.kg * a.n;
+    const int v0 = chain * kChainVec;           // first vector of the chain
+    const uint32_t idesc = tc::idesc_tf32(kM, kChainN);
+    const uint32_t sbo = (kTileK / 4) * 128;
+    volatile int* errv = a.err;
+    for (int s = 0; s < a.steps; ++s) {
+      const int64_t n = a.n0 + s;
+      const int par = (int)(n & 1);
+      if (ctid == 0) {
+        bool got = false;
+        for (uint32_t it = 0; it < kSpinTries; ++it) {
+          if (*errv != 0) break;
+          if (tc::ld_acquire(&ready[2 * j]) >= (int)n && tc::ld_acquire(&ready[2 * j + 1]) >= (int)n) {
+            got = true;
+            break;
+          }
         }
+        if (!got) atomicExch(a.err, 2);
+        tc::fence_proxy_async_global();
+        const float* xt = Xg + (size_t)par * xset + (size_t)j * 2 * kXcFloats;
+        tc::mbar_arrive_expect_tx(bar_x, 4 * 2 * kXcFloats);
+        tc::bulk_g2s(X_hi, xt, 4 * kXcFloats, bar_x);
+        tc::bulk_g2s(X_lo, xt + kXcFloats, 4 * kXcFloats, bar_x);
       }
-      if (!got) atomicExch(a.err, 2);
-      tc::fence_proxy_async_global();
-      const float* xt = a.X + (size_t)par * xset + (size_t)j * 2 * kXTileFloats;
-      tc::mbar_arrive_expect_tx(&bars[1], 4 * 2 * kXTileFloats);
-      tc::bulk_g2s(X_hi, xt, 4 * kXTileFloats, &bars[1]);
-      tc::bulk_g2s(X_lo, xt + kXTileFloats, 4 * kXTileFloats, &bars[1]);
-    }
-    ok = tc::mbar_wait(&bars[1], (uint32_t)(s & 1), kWaitTries) && ok;
-    tc::tc_fence_after();
-    if (tid == 0) {
-      if (ok) {
+      ok = tc::mbar_wait(bar_x, (uint32_t)(s & 1), kWaitTries) && ok;
+      tc::tc_fence_after();
+      if (ctid == 0) {
+        if (ok) {
 #pragma unroll 1
-        for (int ks = 0; ks < kTileK / 8; ++ks) {
-          const uint64_t ah = tc::smem_desc(reinterpret_cast<char*>(A_hi) + ks * 256, 128, sbo);
-          const uint64_t al = tc::smem_desc(reinterpret_cast<char*>(A_lo) + ks * 256, 128, sbo);
-          const uint64_t xh = tc::smem_desc(reinterpret_cast<char*>(X_hi) + ks * 256, 128, sbo);
-          const uint64_t xl = tc::smem_desc(reinterpret_cast<char*>(X_lo) + ks * 256, 128, sbo);
-          tc::mma_tf32(tmem, ah, xh, idesc, ks > 0);
-          tc::mma_tf32(tmem, ah, xl, idesc, true);
-          tc::mma_tf32(tmem, al, xh, idesc, true);
+          for (int ks = 0; ks < kTileK / 8; ++ks) {
+            const uint64_t ah = tc::smem_desc(reinterpret_cast<char*>(A_hi) + ks * 256, 128, sbo);
+            const uint64_t al = tc::smem_desc(reinterpret_cast<char*>(A_lo) + ks * 256, 128, sbo);
+            const uint64_t xh = tc::smem_desc(reinterpret_cast<char*>(X_hi) + ks * 256, 128, sbo);
+            const uint64_t xl = tc::smem_desc(reinterpret_cast<char*>(X_lo) + ks * 256, 128, sbo);
+            tc::mma_tf32(tcol, ah, xh, idesc, ks > 0);
+            tc::mma_tf32(tcol, ah, xl, idesc, true);
+            tc::mma_tf32(tcol, al, xh, idesc, true);
+          }
+          tc::mma_commit(bar_m);
+        } else {
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar_m)) : "memory");
         }
-        tc::mma_commit(&bars[2]);
-      } else {
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bars[2])) : "memory");
       }
-    }
-    ok = tc::mbar_wait(&bars[2], (uint32_t)(s & 1), kWaitTries) && ok;
-    tc::tc_fence_after();
-    float* accb = a.acc + ((size_t)par * MB + mb) * kM * kN;
-    if (warp < 4 && ok) {
-      const int row = 32 * warp + lane;
-#pragma unroll
-      for (int c = 0; c < kN; c += 16) {
+      ok = tc::mbar_wait(bar_m, (uint32_t)(s & 1), kWaitTries) && ok;
+      tc::tc_fence_after();
+      float* accb = accg + ((size_t)par * MB + mb) * kM * kChainN;
+      if (ok) {
+        const int qw = warp & 3;                 // TMEM lane quadrant of this warp
+        const int row = 32 * qw + lane;
         float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c, v);
-        float4* dst = reinterpret_cast<float4*>(accb + row * kN + c);
+        tc::tmem_ld16(tcol + ((uint32_t)(32 * qw) << 16), v);
+        float4* dst = reinterpret_cast<float4*>(accb + row * kChainN);
 #pragma unroll
         for (int q = 0; q < 4; ++q) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
       }
-    }
-    __threadfence();
-    tc::tc_fence_before();
-    __syncthreads();
-    if (tid == 0) *last = (atomicAdd(&a.cnt[par * MB + mb], 1) == a.cs - 1);
-    __syncthreads();
-    if (*last) {
       __threadfence();
-      const cpx<float>* uin = a.u + (size_t)par * rows;
-      cpx<float>* uout = a.u + (size_t)(1 - par) * rows;
-      const cpx<float>* Fs = (a.F != nullptr && n < a.n_forced) ? a.F + (size_t)s * rows : nullptr;
-      cpx<float>* Ys = (a.Y != nullptr && s >= a.y_first) ? a.Y + (size_t)s * rows : nullptr;
-      float* xout = a.X + (size_t)(1 - par) * xset;
-      for (int p = tid; p < kTileRows * 32; p += blockDim.x) {
-        const int iloc = p >> 5;
-        const int v = p & 31;
-        const float pr = __ldcg(accb + iloc * kN + v) - __ldcg(accb + (64 + iloc) * kN + 32 + v);
-        const float pi = __ldcg(accb + iloc * kN + 32 + v) + __ldcg(accb + (64 + iloc) * kN + v);
-        const int i = mb * kTileRows + iloc;
-        if (v < a.kg && i < a.n) {
-          const int64_t e = (int64_t)v * a.n + i;
-          const float2 u0 = __ldcg(reinterpret_cast<const float2*>(uin + e));
-          float2 u1 = make_float2(u0.x + pr, u0.y + pi);
-          if (Fs) {
-            const float2 f = __ldcg(reinterpret_cast<const float2*>(Fs + e));
-            u1.x += f.x;
-            u1.y += f.y;
-          }
-          __stcg(reinterpret_cast<float2*>(uout + e), u1);
-          if (Ys) __stcg(reinterpret_cast<float2*>(Ys + e), u0);
-          const int js = i / kTileK, kk = i % kTileK;
-          float* xo = xout + (size_t)js * 2 * kXTileFloats;
-          const float hr = tc::to_tf32(u1.x), hi = tc::to_tf32(u1.y);
-          const uint32_t o_re = tc::kmajor_offset(v, kk, kTileK) / 4, o_im = tc::kmajor_offset(32 + v, kk, kTileK) / 4;
-          __stcg(xo + o_re, hr);
-          __stcg(xo + kXTileFloats + o_re, u1.x - hr);
-          __stcg(xo + o_im, hi);
-          __stcg(xo + kXTileFloats + o_im, u1.y - hi);
-        }
-      }
-      __syncthreads();
-      for (int e = tid; e < kM * kN / 4; e += blockDim.x)
-        __stcg(reinterpret_cast<float4*>(accb) + e, make_float4(0.f, 0.f, 0.f, 0.f));
-      tc::fence_proxy_async_global();
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) {
-        a.cnt[par * MB + mb] = 0;
+      tc::tc_fence_before();
+      chain_bar(chain);
+      if (ctid == 0) last[chain] = (atomicAdd(&cnt[par * MB + mb], 1) == a.cs - 1);
+      chain_bar(chain);
+      if (last[chain]) {
         __threadfence();
-        tc::st_release(&a.ready[mb], (int)(n + 1));
+        const cpx<float>* uin = a.u + (size_t)par * rows;
+        cpx<float>* uout = a.u + (size_t)(1 - par) * rows;
+        const cpx<float>* Fs = (a.F != nullptr && n < a.n_forced) ? a.F + (size_t)s * rows : nullptr;
+        cpx<float>* Ys = (a.Y != nullptr && s >= a.y_first) ? a.Y + (size_t)s * rows : nullptr;
+        float* xout = Xg + (size_t)(1 - par) * xset;
+        // 64 rows x 8 vectors = 512 (row, vector) pairs, 4 per thread; all loads issued first
+        constexpr int kPairs = kTileRows * kChainVec / 128;
+        const int vl = ctid & 7;
+        const int vg = v0 + vl;
+        float prr[kPairs], pri[kPairs], pir[kPairs], pii[kPairs];
+        float2 u0[kPairs], fv[kPairs];
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+          const int iloc = (ctid >> 3) + 16 * q;
+          prr[q] = __ldcg(accb + iloc * kChainN + vl);
+          pri[q] = __ldcg(accb + iloc * kChainN + kChainVec + vl);
+          pir[q] = __ldcg(accb + (64 + iloc) * kChainN + vl);
+          pii[q] = __ldcg(accb + (64 + iloc) * kChainN + kChainVec + vl);
+          const int64_t e = (int64_t)vg * a.n + mb * kTileRows + iloc;
+          u0[q] = vg < a.kg ? __ldcg(reinterpret_cast<const float2*>(uin + e)) : make_float2(0.f, 0.f);
+          fv[q] = (Fs && vg < a.kg) ? __ldcg(reinterpret_cast<const float2*>(Fs + e)) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+          const int iloc = (ctid >> 3) + 16 * q;
+          const int i = mb * kTileRows + iloc;
+          if (vg < a.kg && i < a.n) {
+            const int64_t e = (int64_t)vg * a.n + i;
+            const float2 u1 = make_float2(u0[q].x + (prr[q] - pii[q]) + fv[q].x, u0[q].y + (pri[q] + pir[q]) + fv[q].y);
+            __stcg(reinterpret_cast<float2*>(uout + e), u1);
+            if (Ys) __stcg(reinterpret_cast<float2*>(Ys + e), u0[q]);
+            const int js = i / kTileK, kk = i % kTileK;
+            float* xo = xout + (size_t)js * 2 * kXcFloats;
+            const float hr = tc::to_tf32(u1.x), hi = tc::to_tf32(u1.y);
+            const uint32_t o_re = tc::kmajor_offset(vl, kk, kTileK) / 4;
+            const uint32_t o_im = tc::kmajor_offset(kChainVec + vl, kk, kTileK) / 4;
+            __stcg(xo + o_re, hr);
+            __stcg(xo + kXcFloats + o_re, u1.x - hr);
+            __stcg(xo + o_im, hi);
+            __stcg(xo + kXcFloats + o_im, u1.y - hi);
+          }
+        }
+        chain_bar(chain);
+        for (int e = ctid; e < kM * kChainN / 4; e += 128)
+          __stcg(reinterpret_cast<float4*>(accb) + e, make_float4(0.f, 0.f, 0.f, 0.f));
+        tc::fence_proxy_async_global();
+        __threadfence();
+        chain_bar(chain);
+        if (ctid == 0) {
+          cnt[par * MB + mb] = 0;
+          tc::st_release(&ready[mb], (int)(n + 1));
+        }
       }
     }
   }
@@ -355,7 +387,7 @@ __global__ void __launch_bounds__(256, 1) dense_tc_march_kernel(TcMarchArgs a) {
   __syncthreads();
   tc::tc_fence_after();
   if (warp == 0) tc::tmem_dealloc(tmem, 64);
-  if (!ok && tid == 0) atomicExch(a.err, 2);
+  if (!ok && (tid & 127) == 0) atomicExch(a.err, 2);
 }
 
 // A tiles from the FP64 matrix (conj-transposed for the adjoint): tile (mb, j) rows
@@ -420,14 +452,14 @@ rsv_status dense_tc_prepare(rsv_operator op, const void* d64_direct) {
   op->tc_persistent = false;
   const int MB = n / kTileRows;
   if (!op->d_ready) {
-    e = cudaMalloc(&op->d_ready, sizeof(int) * (MB + 2 * MB));
+    e = cudaMalloc(&op->d_ready, sizeof(int) * kMaxChains * 3 * MB);
     if (e == cudaSuccess) op->dev.push_back(op->d_ready);
-    if (e == cudaSuccess) e = cudaMalloc(&op->tc_acc, sizeof(float) * 2 * MB * kM * kN);
+    if (e == cudaSuccess) e = cudaMalloc(&op->tc_acc, sizeof(float) * kMaxChains * 2 * MB * kM * kChainN);
     if (e == cudaSuccess) op->dev.push_back(op->tc_acc);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core march buffers");
   }
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_tc_march_kernel, 256, kSmemPersistent);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_tc_march_kernel, 512, kSmemPersistent);
   if (e != cudaSuccess) {
     cudaGetLastError();
     per_sm = 0;
@@ -436,6 +468,11 @@ rsv_status dense_tc_prepare(rsv_operator op, const void* d64_direct) {
   const char* env = getenv("RSV_DENSE_PERSISTENT");
   op->tc_persistent = per_sm * op->sm_count >= MB * cs && !(env != nullptr && env[0] == '0');
   return RSV_OK;
+}
+
+// Operand buffers of the persistent kernel (per chain, two step parities).
+size_t dense_tc_chain_x_bytes(rsv_operator op) {
+  return (size_t)kMaxChains * 2 * (op->n / kTileK) * 2 * kXcFloats * sizeof(float);
 }
 
 // A whole tile of steps in one persistent launch (requires op->tc_persistent).
@@ -448,7 +485,8 @@ cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n
   a.A = (const float*)op->tc_tiles[adjoint ? 1 : 0];
   a.X = (float*)xbuf;
   a.acc = (float*)op->tc_acc;
-  a.cnt = (int*)op->d_ready + MB;
+  a.ready = (int*)op->d_ready;
+  a.cnt = (int*)op->d_ready + kMaxChains * MB;
   a.u = (cpx<float>*)state;
   a.F = (const cpx<float>*)F;
   a.Y = (cpx<float>*)Y;
@@ -459,15 +497,16 @@ cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n
   a.n = n;
   a.kg = kg;
   a.cs = cs;
-  a.ready = (int*)op->d_ready;
+  a.chains = (kg + kChainVec - 1) / kChainVec;
   a.err = op->d_flag;
   cudaError_t e = cudaSuccess;
   if (n0 == 0) {
-    e = cudaMemsetAsync(op->d_ready, 0, sizeof(int) * 3 * MB, op->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(op->tc_acc, 0, sizeof(float) * 2 * MB * kM * kN, op->stream);
+    e = cudaMemsetAsync(op->d_ready, 0, sizeof(int) * kMaxChains * 3 * MB, op->stream);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(op->tc_acc, 0, sizeof(float) * kMaxChains * 2 * MB * kM * kChainN, op->stream);
   }
   if (e != cudaSuccess) return e;
-  dense_tc_march_kernel<<<MB * cs, 256, kSmemPersistent, op->stream>>>(a);
+  dense_tc_march_kernel<<<MB * cs, 512, kSmemPersistent, op->stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -87,9 +87,22 @@ static size_t elem_size(rsv_operator op) { return op->prec == RSV_PREC_FP64 ? 8 
 // Extra march scratch that lives behind the state vector in the state workspace.
 size_t stage_scratch_bytes(rsv_operator op, int kg) {
   if (op->kind == RSV_OP_DENSE)  // second state buffer, then the tensor-core operand buffers
-    return (size_t)kg * op->n * 2 * elem_size(op) + (dense_tc_supported(op, kg) ? dense_tc_scratch_bytes(op) : 0);
+    return (size_t)kg * op->n * 2 * elem_size(op) +
+           (dense_tc_supported(op, kg) ? std::max(dense_tc_scratch_bytes(op), dense_tc_chain_x_bytes(op)) : 0);
   if (op->kind == RSV_OP_ADR2D || op->kind == RSV_OP_ADV3D) return stencil_scratch_bytes(op, kg);
   return 0;
+}
+
+int march_tile_kernels(rsv_operator op, int steps, int kg) {
+  switch (op->kind) {
+    case RSV_OP_GL1D:
+      return 1;
+    case RSV_OP_DENSE:
+      if (op->prec == RSV_PREC_FP32 && dense_tc_supported(op, kg)) return op->tc_persistent ? 2 : steps + 1;
+      return steps + 1;
+    default:
+      return 4 * steps + 1;
+  }
 }
 
 rsv_status on_frequencies(rsv_operator op) {

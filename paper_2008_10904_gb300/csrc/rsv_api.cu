@@ -74,12 +74,13 @@ static void prof_flush(rsv_operator op) {
     if (cudaEventElapsedTime(&t, p.pool[2 * i], p.pool[2 * i + 1]) == cudaSuccess) {
       p.ms[p.cat[i]] += t;
       p.launches[p.cat[i]] += 1;
+      p.kernels[p.cat[i]] += p.nk[i];
     }
   }
   p.used = 0;
 }
 
-ProfScope::ProfScope(rsv_operator o, int c) : op(o), cat(c) {
+ProfScope::ProfScope(rsv_operator o, int c, int nkernels) : op(o), cat(c) {
   Profiler& p = op->prof;
   if (!p.on) return;
   if (p.used >= 4096) prof_flush(op);
@@ -90,8 +91,10 @@ ProfScope::ProfScope(rsv_operator o, int c) : op(o), cat(c) {
       p.pool.push_back(e);
     }
     p.cat.push_back(0);
+    p.nk.push_back(0);
   }
   p.cat[p.used] = c;
+  p.nk[p.used] = nkernels;
   cudaEventRecord(p.pool[2 * p.used], op->stream);
 }
 
@@ -134,15 +137,18 @@ extern "C" rsv_status rsv_profile_reset(rsv_operator op) {
   prof_flush(op);
   for (int c = 0; c < 4; ++c) {
     op->prof.launches[c] = 0;
+    op->prof.kernels[c] = 0;
     op->prof.ms[c] = 0.0;
   }
   return RSV_OK;
 }
 
-extern "C" rsv_status rsv_profile_read(rsv_operator op, int32_t category, int64_t* launches, double* ms) {
+extern "C" rsv_status rsv_profile_read(rsv_operator op, int32_t category, int64_t* groups, int64_t* kernels,
+                                       double* ms) {
   if (!op || category < 0 || category > 3) return fail(RSV_ERR_INVALID_ARG, "bad profile query");
   prof_flush(op);
-  if (launches) *launches = op->prof.launches[category];
+  if (groups) *groups = op->prof.launches[category];
+  if (kernels) *kernels = op->prof.kernels[category];
   if (ms) *ms = op->prof.ms[category];
   return RSV_OK;
 }
@@ -440,7 +446,7 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
     const void* fh = nullptr;
     int synth_stride = 1;
     {
-      ProfScope ps(op, PROF_GLUE);
+      ProfScope ps(op, PROF_GLUE, op->kind == RSV_OP_DENSE ? (kv == k ? 3 : 2 * op->n_omega + 1) : 0);
       st = prepare_coefficients<R>(op, static_cast<const char*>(in) + (size_t)v0 * n * ce, (int64_t)k * n, kv, adjoint,
                                    &fh, &g.coef_stride, &synth_stride);
     }
@@ -466,7 +472,7 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
       mt.kg = kv;
       mt.adjoint = adjoint;
       {
-        ProfScope ps(op, PROF_MARCH);
+        ProfScope ps(op, PROF_MARCH, march_tile_kernels(op, g.steps, kv));
         e = march_tile<R>(op, mt, op->ws_state.ptr, forced ? op->ws_ftile.ptr : nullptr,
                           analysed ? op->ws_ysnap.ptr : nullptr, (double*)op->ws_norm.ptr);
       }

@@ -81,7 +81,9 @@ struct Profiler {
   std::vector<cudaEvent_t> pool;
   std::vector<int> cat;  // category of each recorded pair (events 2i, 2i+1)
   size_t used = 0;
+  std::vector<int> nk;   // kernels launched inside each recorded pair
   int64_t launches[4] = {0, 0, 0, 0};
+  int64_t kernels[4] = {0, 0, 0, 0};
   double ms[4] = {0, 0, 0, 0};
 };
 
@@ -157,7 +159,7 @@ rsv_status ensure(Workspace& w, size_t bytes);
 struct ProfScope {
   rsv_operator op;
   int cat;
-  ProfScope(rsv_operator o, int c);
+  ProfScope(rsv_operator o, int c, int nkernels = 1);
   ~ProfScope();
 };
 enum { PROF_SYNTH = 0, PROF_MARCH = 1, PROF_ANALYSIS = 2, PROF_GLUE = 3 };

@@ -23,6 +23,9 @@ rsv_status upload(rsv_operator op, const void* host, size_t bytes, void** dst);
 int default_tile_steps(rsv_operator op);
 size_t stage_scratch_bytes(rsv_operator op, int kg);
 
+// Number of kernels one march_tile call launches (for the launch accounting).
+int march_tile_kernels(rsv_operator op, int steps, int kg);
+
 // S RK4 steps of the operator's stage kernel(s) on the state block (kg vectors).
 template <typename R>
 cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const void* F, void* Y, double* norms);
@@ -56,6 +59,7 @@ size_t dense_tc_scratch_bytes(rsv_operator op);
 rsv_status dense_tc_prepare(rsv_operator op, const void* d64_direct);
 cudaError_t dense_tc_step(rsv_operator op, int kg, bool adjoint, int64_t step, const void* uin, void* uout,
                           const void* F, void* Y, void* xbuf);
+size_t dense_tc_chain_x_bytes(rsv_operator op);
 cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n0, int steps, int64_t n_forced,
                                 int y_first, void* state, const void* F, void* Y, void* xbuf);
 

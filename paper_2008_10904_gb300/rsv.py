@@ -77,7 +77,7 @@ _ENTRY_POINTS = {
     "rsv_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "rsv_profile_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "rsv_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
-                                        ctypes.POINTER(ctypes.c_double)]),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "rsv_describe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]),
     "rsv_last_error": (ctypes.c_char_p, []),
     "rsv_version": (ctypes.c_char_p, []),
@@ -217,9 +217,10 @@ def rsv_profile_reset(op: Operator):
 
 
 def rsv_profile_read(op: Operator, category: int):
-    n, ms = ctypes.c_int64(), ctypes.c_double()
-    _check(_lib.rsv_profile_read(op.handle, int(category), ctypes.byref(n), ctypes.byref(ms)))
-    return n.value, ms.value
+    """(bracketed groups, kernels launched, summed event ms) of one category."""
+    g, n, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(_lib.rsv_profile_read(op.handle, int(category), ctypes.byref(g), ctypes.byref(n), ctypes.byref(ms)))
+    return g.value, n.value, ms.value
 
 
 def rsv_describe(op: Operator) -> str:
