@@ -159,7 +159,7 @@ FP64_ALU_TFLOPS = 1.25                                # nominal FP64 rate of the
 def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
     """Roofline record of one kernel category: algorithmic work per launch / average launch time.
 
-    Units of work per launch (one time tile of S steps, see the design notes):
+    Units of work per launch (one time tile of S steps):
       synthesis  rows x n_omega x n_tau complex (8 flop) or real-output (4 flop) multiply-adds
       analysis   rows x n_omega x S multiply-adds (8 flop complex state, 4 flop real state)
       march      dense: 8 n^2 k flop per step (one dense complex product, tensor cores);

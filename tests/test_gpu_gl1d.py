@@ -2,8 +2,10 @@
 
 Element-by-element comparison of the CUDA marches (through the C ABI) with
 the oracle's march on the same seeded inputs: FP64 path within 1e-10
-relative, FP32 path within the FP32 tolerance derived in the design notes.
-Sizes span several time tiles with ragged last tiles.
+relative to the block maximum; FP32 path within 2e-5 (FP32 rounding of
+~6e-8 per operation, amplified by gains of order 10-30 and by the 64-step
+FP32 partial sums of the DFT, stays at a few 1e-6).  Sizes span several
+time tiles with ragged last tiles.
 """
 import numpy as np
 import pytest
