@@ -173,15 +173,22 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
     se = (8 if prec == "fp64" else 4) * (1 if w.real_state else 2)
     alu_peak = FP64_ALU_TFLOPS if prec == "fp64" else FP32_ALU_TFLOPS
     cflop = 4 if w.real_state else 8
+    tc_contract = "contractions=tcgen05" in path
+    if cat in ("synthesis", "analysis") and tc_contract:
+        peak_tc = peaks["bf16_tflops"] * 1.1 / 2.25
     if cat == "synthesis":
         n_tau = S if dense else 2 * S + 1
         work = rows * w.n_omega * n_tau * cflop
         bound, unit, peak, per = "alu", "TFLOP/s", alu_peak, 1e12
         src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if prec != "fp64" else "nominal FP64"
+        if tc_contract:
+            bound, peak, src = "tensor", peak_tc, "measured bf16 x nominal tf32/bf16 ratio (1.1/2.25)"
     elif cat == "analysis":
         work = rows * w.n_omega * S * cflop
         bound, unit, peak, per = "alu", "TFLOP/s", alu_peak, 1e12
         src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if prec != "fp64" else "nominal FP64"
+        if tc_contract:
+            bound, peak, src = "tensor", peak_tc, "measured bf16 x nominal tf32/bf16 ratio (1.1/2.25)"
     elif cat == "march" and dense and "tcgen05" in path:
         work = 8.0 * w.n * w.n * w.k * S
         peak = peaks["bf16_tflops"] * 1.1 / 2.25
@@ -353,9 +360,11 @@ def run_ours(args):
     elif prec_name == "fp64":
         acc = {"gain_rel_err_max": 0.0, "vs": "FP64 path itself (parity-tested against the oracle to 1e-10)"}
 
+    path = rsv.rsv_describe(op)   # now includes the tile / group sizes the marches used
     dom = max(prof, key=lambda c: prof[c][2])
-    rows = w.k * w.n
-    tile = args.tile or 256
+    desc = dict(kv.split("=", 1) for kv in path.split() if "=" in kv)
+    tile = int(desc.get("tile", args.tile or 256))
+    rows = int(desc.get("group", w.k)) * w.n
     roof = kernel_model(dom, w, prec_name, tile, prof[dom][0], prof[dom][2], rows, path)
     launches = sum(v[1] for v in prof.values())
     steps_per_march = {"ssrm": (w.n_transient_windows + 1) * n_t, "trm": n_t + w.tail_steps}[w.variant]

@@ -80,7 +80,12 @@ rsv_status build_gl1d(rsv_operator op, const rsv_operator_desc* d) {
 }
 
 
-int default_tile_steps(rsv_operator op) { return 256; }
+// Default time-tile length: 256 steps, trimmed in FP32 so one tile's stage times fit the
+// tensor-core synthesis accumulator (<= 512 columns): 2S + 1 <= 512 real, 2 (2S + 1) <= 512 complex.
+int default_tile_steps(rsv_operator op) {
+  if (op->prec != RSV_PREC_FP32 || op->kind == RSV_OP_DENSE) return 256;
+  return op->real_state ? 255 : 127;
+}
 
 static size_t elem_size(rsv_operator op) { return op->prec == RSV_PREC_FP64 ? 8 : 4; }
 

@@ -115,7 +115,8 @@ using namespace rsv;
 
 rsv_operator_s::~rsv_operator_s() {
   for (void* p : dev) cudaFree(p);
-  Workspace* ws[] = {&ws_state, &ws_ftile, &ws_ysnap, &ws_acc, &ws_norm, &ws_glue_a, &ws_glue_b, &ws_gram, &ws_small};
+  Workspace* ws[] = {&ws_state, &ws_ftile, &ws_ysnap, &ws_acc, &ws_norm, &ws_glue_a, &ws_glue_b,
+                     &ws_gram,  &ws_small, &ws_coef,  &ws_coef2, &ws_tcb};
   for (Workspace* w : ws)
     if (w->ptr) cudaFree(w->ptr);
   if (d_tw) cudaFree(d_tw);
@@ -171,6 +172,9 @@ extern "C" rsv_status rsv_create_operator(const rsv_operator_desc* d, void* stre
     // RSV_DENSE_TENSOR=0 keeps dense FP32 operators on the CUDA-core step (for comparisons)
     const char* env = getenv("RSV_DENSE_TENSOR");
     op->tc_disabled = env != nullptr && env[0] == '0';
+    // RSV_CONTRACT_TENSOR=0 keeps FP32 synthesis / analysis on the CUDA cores (for comparisons)
+    const char* env2 = getenv("RSV_CONTRACT_TENSOR");
+    op->tc_contract_disabled = env2 != nullptr && env2[0] == '0';
   }
   int dev = 0;
   cudaGetDevice(&dev);
@@ -223,9 +227,13 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
     else
       path = "cuda-core propagator step";
   }
-  snprintf(buf, (size_t)buflen, "kind=%s precision=%s n=%lld instances=%d path=%s resident_ctas=%d sms=%d",
+  const char* contract = (op->prec == RSV_PREC_FP32 && !op->tc_contract_disabled) ? "tcgen05" : "cuda-core";
+  snprintf(buf, (size_t)buflen,
+           "kind=%s precision=%s n=%lld instances=%d path=%s contractions=%s resident_ctas=%d sms=%d tile=%d "
+           "group=%d",
            (op->kind >= 0 && op->kind < 4) ? kinds[op->kind] : "?", op->prec == RSV_PREC_FP64 ? "fp64" : "fp32",
-           (long long)op->n, op->n_inst, path, op->tc_max_clusters, op->sm_count);
+           (long long)op->n, op->n_inst, path, contract, op->tc_max_clusters, op->sm_count, op->last_tile,
+           op->last_group);
   return RSV_OK;
 }
 
@@ -381,8 +389,9 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
   if (st != RSV_OK) return st;
   const int64_t n = op->n;
   const size_t se = state_elem_bytes(op);
-  // Tile length S and vector-group size kg: the requested / default tile, shrunk (S down to 16,
-  // then kg halved) until the march workspace fits in 90% of the device memory not held by others.
+  // Tile length S and vector-group size kg: the requested / default tile and all k vectors, shrunk
+  // (kg halved, then S down to 16) until the march workspace fits in 90% of the device memory not
+  // held by others.
   int S = (opts && opts->tile_steps > 0) ? opts->tile_steps : default_tile_steps(op);
   int kg = k;
   {
@@ -401,15 +410,19 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
       if (op->kind == RSV_OP_DENSE) b += 2.0 * op->n_omega * rows_ * 2 * sizeof(R);
       return b;
     };
+    // per-tile traffic (coefficients, FP64 accumulators) is amortised over S, while the vector
+    // group only sets how much is resident: shrink the group first, then the tile
     while (need(S, kg) > budget && (S > 16 || kg > 1)) {
-      if (S > 16)
-        S = std::max(16, S / 2);
-      else
+      if (kg > 1)
         kg = (kg + 1) / 2;
+      else
+        S = std::max(16, S / 2);
     }
   }
   const cudaStream_t stream = op->stream;
   cudaError_t e;
+  op->last_tile = S;
+  op->last_group = kg;
   const int64_t rows_max = (int64_t)kg * n;
   if ((st = ensure(op->ws_state, rows_max * se + stage_scratch_bytes(op, kg))) != RSV_OK) return st;
   if ((st = ensure(op->ws_ftile, (size_t)(2 * S + 1) * rows_max * se)) != RSV_OK) return st;
@@ -459,8 +472,15 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
       const bool forced = n0 < sc.forced;
       const bool analysed = n0 + g.steps > sc.first;
       if (forced) {
-        ProfScope ps(op, PROF_SYNTH);
-        e = launch_synth<R>(g, fh, op->d_tw, op->d_pj, op->d_cw, op->real_state, op->ws_ftile.ptr, stream);
+        if (sizeof(R) == 4 && tc_contract_supported(op, true)) {
+          const int nt = g.n_tau > 0 ? g.n_tau : 2 * g.steps + 1;
+          const int calls = (nt + (op->real_state ? 511 : 255)) / (op->real_state ? 512 : 256);
+          ProfScope ps(op, PROF_SYNTH, 2 * calls);
+          e = tc_synth(op, g, fh, op->ws_ftile.ptr);
+        } else {
+          ProfScope ps(op, PROF_SYNTH);
+          e = launch_synth<R>(g, fh, op->d_tw, op->d_pj, op->d_cw, op->real_state, op->ws_ftile.ptr, stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "synthesis");
       }
       const int y_first = analysed ? (int)std::max<int64_t>(0, sc.first - n0) : g.steps;
@@ -478,9 +498,14 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
       }
       if (e != cudaSuccess) return cuda_fail(e, "march tile");
       if (analysed) {
-        ProfScope ps(op, PROF_ANALYSIS);
-        e = launch_analysis<R>(g, op->ws_ysnap.ptr, y_first, g.steps, op->d_tw, op->d_pj, op->real_state, acc,
-                               acc_stride, stream);
+        if (sizeof(R) == 4 && tc_contract_supported(op, false)) {
+          ProfScope ps(op, PROF_ANALYSIS, 2);
+          e = tc_analysis(op, g, op->ws_ysnap.ptr, y_first, g.steps, acc, acc_stride);
+        } else {
+          ProfScope ps(op, PROF_ANALYSIS);
+          e = launch_analysis<R>(g, op->ws_ysnap.ptr, y_first, g.steps, op->d_tw, op->d_pj, op->real_state, acc,
+                                 acc_stride, stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "analysis");
       }
     }

@@ -141,9 +141,11 @@ struct rsv_operator_s {
 
   // march workspace (grown on demand)
   rsv::Workspace ws_state, ws_ftile, ws_ysnap, ws_acc, ws_norm, ws_glue_a, ws_glue_b, ws_gram, ws_small;
-  rsv::Workspace ws_coef, ws_coef2;
+  rsv::Workspace ws_coef, ws_coef2, ws_tcb;
+  bool tc_contract_disabled = false;   // keep the synthesis / analysis on the CUDA cores
   int* d_flag = nullptr;
   rsv::Profiler prof;
+  int last_tile = 0, last_group = 0;   // tile length and vector-group size of the latest march
 
   ~rsv_operator_s();
 };
@@ -191,6 +193,12 @@ template <typename R>
 cudaError_t launch_finish(const cpx<double>* acc, int64_t acc_stride, int n_omega, int64_t rows,
                           double scale, void* out, int64_t out_stride, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+// ----- tensor-core contractions (tc_contract.cu), FP32 mode -----------------
+bool tc_contract_supported(rsv_operator op, bool synth);
+cudaError_t tc_synth(rsv_operator op, const TileGeom& g, const void* fhat, void* F);
+cudaError_t tc_analysis(rsv_operator op, const TileGeom& g, const void* Y, int s0, int s1, cpx<double>* acc,
+                        int64_t acc_stride);
 
 // ----- GL1D (gl1d_kernels.cu) ---------------------------------------------
 struct Gl1dTile {

@@ -170,6 +170,158 @@ __global__ void __launch_bounds__(256) adv3d_stage_kernel(StGeom g, const R* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 stage kernels, four consecutive x cells per thread (float4 loads and
+// stores along x; the x neighbours of the group come from two scalar loads).
+// Used when nx is a multiple of 4.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float get4(const float4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
+__device__ __forceinline__ void set4(float4& v, int q, float x) {
+  if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
+}
+
+template <int STAGE>
+__device__ __forceinline__ void stage_update4(int64_t p, float4 k, const float* __restrict__ u, float* __restrict__ acc,
+                                              float* __restrict__ xout, float* __restrict__ ysnap, float h) {
+  if (STAGE == 1) {
+    const float4 uu = ld4(u + p);
+    if (ysnap) st4(ysnap + p, uu);
+    st4(xout + p, make_float4(uu.x + 0.5f * h * k.x, uu.y + 0.5f * h * k.y, uu.z + 0.5f * h * k.z, uu.w + 0.5f * h * k.w));
+    const float c = h / 6.f;
+    st4(acc + p, make_float4(uu.x + c * k.x, uu.y + c * k.y, uu.z + c * k.z, uu.w + c * k.w));
+  } else if (STAGE == 2 || STAGE == 3) {
+    const float4 uu = ld4(u + p);
+    const float cx = STAGE == 2 ? 0.5f * h : h;
+    st4(xout + p, make_float4(uu.x + cx * k.x, uu.y + cx * k.y, uu.z + cx * k.z, uu.w + cx * k.w));
+    float4 a = ld4(acc + p);
+    const float c = h / 3.f;
+    st4(acc + p, make_float4(a.x + c * k.x, a.y + c * k.y, a.z + c * k.z, a.w + c * k.w));
+  } else {
+    const float4 a = ld4(acc + p);
+    const float c = h / 6.f;
+    st4(xout + p, make_float4(a.x + c * k.x, a.y + c * k.y, a.z + c * k.z, a.w + c * k.w));
+  }
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(256) adr2d_stage4_kernel(StGeom g, const float* __restrict__ xin,
+                                                           const float* __restrict__ u, float* __restrict__ acc,
+                                                           const float* __restrict__ f, float* xout,
+                                                           float* __restrict__ ysnap, float h) {
+  const int i0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  const int v = blockIdx.z;
+  if (i0 >= g.nx || j >= g.ny) return;
+  const int nx = g.nx, ny = g.ny;
+  const int64_t base = (int64_t)v * g.n;
+  const float* xv = xin + base;
+  const int64_t row = (int64_t)j * nx;
+  const float4 c = ld4(xv + row + i0);
+  const float w = i0 > 0 ? xv[row + i0 - 1] : 0.f;
+  const float e = i0 + 4 < nx ? xv[row + i0 + 4] : 0.f;
+  const float4 sv = j > 0 ? ld4(xv + row - nx + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 nv = j < ny - 1 ? ld4(xv + row + nx + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* U = reinterpret_cast<const float*>(g.f0);
+  const float* rr = reinterpret_cast<const float*>(g.f1);
+  const float ux = g.adjoint ? -U[j] : U[j];
+  const float idx2 = 1.f / ((float)g.dx * (float)g.dx), idy2 = 1.f / ((float)g.dy * (float)g.dy);
+  const float i2dx = 0.5f / (float)g.dx, nu = (float)g.visc;
+  const float cw = ux * i2dx + nu * idx2, ce = -ux * i2dx + nu * idx2, cy = nu * idy2;
+  const float cc0 = -2.f * nu * (idx2 + idy2) + rr[j];
+  float4 k;
+  const float4 fv = f ? ld4(f + base + row + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float left = q == 0 ? w : get4(c, q - 1);
+    const float right = q == 3 ? e : get4(c, q + 1);
+    const float cc = cc0 - sponge<float>(i0 + q, j, g);
+    set4(k, q, cw * left + ce * right + cy * (get4(sv, q) + get4(nv, q)) + cc * get4(c, q) + get4(fv, q));
+  }
+  stage_update4<STAGE>(base + row + i0, k, u, acc, xout, ysnap, h);
+}
+
+// Blocks are ordered with the vector index fastest, so the base-flow fields of a
+// cell block are read from HBM once and served from L2 to the other vectors.
+template <int STAGE>
+__global__ void __launch_bounds__(256) adv3d_stage4_kernel(StGeom g, const float* __restrict__ xin,
+                                                           const float* __restrict__ u, float* __restrict__ acc,
+                                                           const float* __restrict__ f, float* xout,
+                                                           float* __restrict__ ysnap, float h) {
+  const int v = blockIdx.x % g.kg;
+  const int cb = blockIdx.x / g.kg;
+  const int nxb = (g.nx / 4 + 31) / 32;
+  const int i0 = 4 * ((cb % nxb) * 32 + threadIdx.x);
+  const int jz = (cb / nxb) * 8 + threadIdx.y;
+  if (i0 >= g.nx || jz >= g.ny * g.nz) return;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int j = jz % ny, kz = jz / ny;
+  const int64_t base = (int64_t)v * g.n;
+  const int64_t ncell = (int64_t)nx * ny * nz;
+  const int64_t q0 = ((int64_t)kz * ny + j) * nx + i0;
+  const float* U = reinterpret_cast<const float*>(g.f0);
+  const float* Ux = reinterpret_cast<const float*>(g.f1);
+  const float* Uy = reinterpret_cast<const float*>(g.f2);
+  const float* Uz = reinterpret_cast<const float*>(g.f3);
+  const float idx2 = 1.f / ((float)g.dx * (float)g.dx), idy2 = 1.f / ((float)g.dy * (float)g.dy);
+  const float idz2 = 1.f / ((float)g.dz * (float)g.dz), i2dx = 0.5f / (float)g.dx, nu = (float)g.visc;
+  const float4 U4 = ld4(U + q0);
+  const float Uw = i0 > 0 ? U[q0 - 1] : 0.f, Ue = i0 + 4 < nx ? U[q0 + 4] : 0.f;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 xc[3], k[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* x = xin + base + c * ncell;
+    const float4 cv = ld4(x + q0);
+    const float w = i0 > 0 ? x[q0 - 1] : 0.f;
+    const float e = i0 + 4 < nx ? x[q0 + 4] : 0.f;
+    const float4 sv = j > 0 ? ld4(x + q0 - nx) : zero;
+    const float4 nv = j < ny - 1 ? ld4(x + q0 + nx) : zero;
+    const float4 bv = kz > 0 ? ld4(x + q0 - (int64_t)nx * ny) : zero;
+    const float4 tv = kz < nz - 1 ? ld4(x + q0 + (int64_t)nx * ny) : zero;
+    xc[c] = cv;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float left = q == 0 ? w : get4(cv, q - 1);
+      const float right = q == 3 ? e : get4(cv, q + 1);
+      const float cc = get4(cv, q);
+      float adv;
+      if (g.adjoint) {
+        const float ul = q == 0 ? Uw : get4(U4, q - 1);
+        const float ur = q == 3 ? Ue : get4(U4, q + 1);
+        adv = (ur * right - ul * left) * i2dx;
+      } else {
+        adv = -get4(U4, q) * (right - left) * i2dx;
+      }
+      set4(k[c], q, adv + nu * (idx2 * (left + right - 2.f * cc) + idy2 * (get4(sv, q) + get4(nv, q) - 2.f * cc) +
+                               idz2 * (get4(bv, q) + get4(tv, q) - 2.f * cc)));
+    }
+  }
+  const float4 gx = ld4(Ux + q0), gy = ld4(Uy + q0), gz = ld4(Uz + q0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float x0 = get4(xc[0], q), x1 = get4(xc[1], q), x2 = get4(xc[2], q);
+    if (g.adjoint) {
+      set4(k[0], q, get4(k[0], q) - get4(gx, q) * x0);
+      set4(k[1], q, get4(k[1], q) - get4(gy, q) * x0);
+      set4(k[2], q, get4(k[2], q) - get4(gz, q) * x0);
+    } else {
+      set4(k[0], q, get4(k[0], q) - (get4(gx, q) * x0 + get4(gy, q) * x1 + get4(gz, q) * x2));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int64_t p = base + c * ncell + q0;
+    float4 kc = k[c];
+    if (f) {
+      const float4 fv = ld4(f + p);
+      kc = make_float4(kc.x + fv.x, kc.y + fv.y, kc.z + fv.z, kc.w + fv.w);
+    }
+    stage_update4<STAGE>(p, kc, u, acc, xout, ysnap, h);
+  }
+}
+
 template <typename R>
 __global__ void adr2d_apply_real_kernel(StGeom g, const R* __restrict__ x, R* __restrict__ y) {
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -249,6 +401,23 @@ StGeom geom_of(rsv_operator op, int kg, bool adjoint) {
 template <typename R, int STAGE>
 cudaError_t launch_stage(rsv_operator op, const StGeom& g, const R* xin, const R* u, R* acc, const R* f, R* xout,
                          R* ysnap, R h) {
+  if (sizeof(R) == 4 && g.nx % 4 == 0) {
+    const float* xi = reinterpret_cast<const float*>(xin);
+    const float* uu = reinterpret_cast<const float*>(u);
+    float* ac = reinterpret_cast<float*>(acc);
+    const float* ff = reinterpret_cast<const float*>(f);
+    float* xo = reinterpret_cast<float*>(xout);
+    float* ys = reinterpret_cast<float*>(ysnap);
+    const unsigned gx = (unsigned)((g.nx / 4 + 31) / 32);
+    if (op->kind == RSV_OP_ADR2D) {
+      dim3 grid(gx, (unsigned)((g.ny + 7) / 8), (unsigned)g.kg);
+      adr2d_stage4_kernel<STAGE><<<grid, dim3(32, 8), 0, op->stream>>>(g, xi, uu, ac, ff, xo, ys, (float)h);
+    } else {
+      const unsigned blocks = gx * (unsigned)((g.ny * g.nz + 7) / 8) * (unsigned)g.kg;
+      adv3d_stage4_kernel<STAGE><<<blocks, dim3(32, 8), 0, op->stream>>>(g, xi, uu, ac, ff, xo, ys, (float)h);
+    }
+    return cudaGetLastError();
+  }
   if (op->kind == RSV_OP_ADR2D) {
     dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 7) / 8), (unsigned)g.kg);
     adr2d_stage_kernel<R, STAGE><<<grid, dim3(32, 8), 0, op->stream>>>(g, xin, u, acc, f, xout, ysnap, h);

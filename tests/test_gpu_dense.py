@@ -77,7 +77,9 @@ def test_dense_march_fp64(rsv, variant, tile, adjoint):
 
 
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_dense_march_fp32(rsv, adjoint):
+@pytest.mark.parametrize("contract", ["tensor", "cuda_cores"])
+def test_dense_march_fp32(rsv, adjoint, contract, monkeypatch):
+    monkeypatch.setenv("RSV_CONTRACT_TENSOR", "1" if contract == "tensor" else "0")
     w = _small("trm", k=4)
     a = W.hermite_gl_matrix(w.system)
     op = rsv.create_for_workload(w, 1, dense_matrix=a)

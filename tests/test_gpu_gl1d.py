@@ -81,7 +81,9 @@ def test_march_fp64_matches_oracle(rsv, variant, tile, adjoint):
 
 
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_march_fp32_matches_oracle(rsv, adjoint):
+@pytest.mark.parametrize("contract", ["tensor", "cuda_cores"])
+def test_march_fp32_matches_oracle(rsv, adjoint, contract, monkeypatch):
+    monkeypatch.setenv("RSV_CONTRACT_TENSOR", "1" if contract == "tensor" else "0")
     w = W.small_gl(n=200, n_omega=16, k=4, n_trans=3, mu0=-0.1, dt=0.005, x_half=40.0)
     op = rsv.create_for_workload(w, rsv.RSV_PREC_FP32)
     try:

@@ -37,6 +37,15 @@ def _adr_small(variant="ssrm", omegas=None, k=3):
                       n_power_iter=1, real_state=True, seed=W.SEED_BASE + 33)
 
 
+def _adr_odd(variant="ssrm", omegas=None, k=3):
+    """nx not a multiple of 4: the scalar stage kernels."""
+    sysm = W.ADR2D(nx=42, ny=22, lx=40.0, ly=10.0, sponge_cells=4)
+    om = np.linspace(0.0, 4.0, 8) if omegas is None else omegas
+    dx = sysm.lx / (sysm.nx + 1)
+    return W.Workload("adr_odd", sysm, om, 0.5 * dx, k, variant, n_transient_windows=2, tail_steps=60,
+                      n_power_iter=1, real_state=True, seed=W.SEED_BASE + 34)
+
+
 def _adv_small(variant="ssrm", k=2):
     sysm = W.ADV3D(nx=12, ny=8, nz=6, lx=20.0, ly=10.0, lz=10.0, visc=0.02)
     om = np.array([0.04 * np.pi * 5 * j for j in range(6)])
@@ -92,9 +101,12 @@ def test_stencil_march_fp64(rsv, make, variant, tile, adjoint):
         rsv.rsv_destroy_operator(op)
 
 
-@pytest.mark.parametrize("make", [_adr_small, _adv_small])
+@pytest.mark.parametrize("make", [_adr_small, _adr_odd, _adv_small])
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_stencil_march_fp32(rsv, make, adjoint):
+@pytest.mark.parametrize("contract", ["tensor", "cuda_cores"])
+def test_stencil_march_fp32(rsv, make, adjoint, contract, monkeypatch):
+    """FP32 march with the synthesis / analysis on the tensor cores and on the CUDA cores."""
+    monkeypatch.setenv("RSV_CONTRACT_TENSOR", "1" if contract == "tensor" else "0")
     w = make("trm")
     op = rsv.create_for_workload(w, 1)
     try:

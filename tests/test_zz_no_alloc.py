@@ -16,7 +16,7 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10
-TOL32 = 1e-6
+TOL32 = 2e-5   # the FP32 march tolerance of the other parity tests (contractions may run on different units)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
