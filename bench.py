@@ -152,6 +152,12 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
 
 
+# DRAM bytes (read + write) per launch of a category's kernels over one time tile, from one
+# ncu capture of the same kernels at the same tile length and rows per launch, keyed by
+# (workload, category, tile steps, rows per launch).  An entry is dropped whenever the
+# kernel it describes changes.
+TRAFFIC = {}
+
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 FP64_ALU_TFLOPS = 1.25                                # nominal FP64 rate of the part
 
@@ -163,8 +169,11 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
       synthesis  rows x n_omega x n_tau complex (8 flop) or real-output (4 flop) multiply-adds
       analysis   rows x n_omega x S multiply-adds (8 flop complex state, 4 flop real state)
       march      dense: 8 n^2 k flop per step (one dense complex product, tensor cores);
-                 1-D and stencil kinds: state bytes the RK4 stages must move, 14 state passes
-                 per step (12 for four stage read/write pairs, 2 for the forcing) + 1 snapshot
+                 1-D kind (state held on chip for the whole tile): the forcing tile read
+                 (2S+1 stage times), the snapshot tile written (S steps) and the state read
+                 and written once, (3S + 3) state passes per tile;
+                 stencil kinds: 15 state passes per step (12 for four stage read/write
+                 pairs, 2 forcing reads, 1 snapshot write)
     """
     peaks = load_peaks()
     avg_s = ms_total / max(groups, 1) / 1e3
@@ -198,14 +207,19 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
         work = 8.0 * w.n * w.n * w.k * S
         bound, unit, peak, per = "alu", "TFLOP/s", alu_peak, 1e12
         src = "derived FP32 CUDA-core rate"
+    elif cat == "march" and "kind=gl1d" in path:
+        work = (3.0 * S + 3.0) * rows * se
+        bound, unit, peak, per = "hbm", "GB/s", peaks["hbm_gbs"], 1e9
+        src = peaks["src"] + " copy bandwidth"
     else:
         work = 15.0 * rows * se * S
         bound, unit, peak, per = "hbm", "GB/s", peaks["hbm_gbs"], 1e9
         src = peaks["src"] + " copy bandwidth"
     achieved = work / avg_s / per
+    traffic = TRAFFIC.get((w.name, cat, S, rows))
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-            "traffic": None, "kernel": cat, "work_per_launch": work, "avg_launch_ms": avg_s * 1e3,
-            "peak_src": src}
+            "traffic": traffic["bytes"] if traffic else None, "traffic_src": traffic["src"] if traffic else None,
+            "kernel": cat, "work_per_launch": work, "avg_launch_ms": avg_s * 1e3, "peak_src": src}
 
 
 # ---------------------------------------------------------------------------
@@ -235,6 +249,10 @@ print(json.dumps({{"seconds": dt, "steps": steps, "total_steps": int(total), "fi
 
 def cpu_baseline(name: str, target_seconds: float = 15.0):
     w = workload(name)
+    if w.n * w.k * w.n_omega > (1 << 31):
+        return {"value": None, "unit": "actions/s", "cores": 1, "kind": "oracle",
+                "sample": f"not run: the FP64 oracle would hold {w.n * w.k * w.n_omega * 16 / 2**30:.0f} GiB "
+                          "of complex128 test block and accumulators on the host"}
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     probe = 10 if type(w.system).__name__ in ("Dense", "ADV3D") else 100
     r = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, name=name, steps=probe)],
@@ -290,8 +308,16 @@ def run_ours(args):
     n_t, h = rsv.rsv_set_frequencies(op, w.omegas)
     path = rsv.rsv_describe(op)
     opts = rsv.march_opts_for(w, tile_steps=args.tile)
-    omega_host = W.test_block(w, seed_offset=rank_seed_offset(rank))
-    omega_dev = torch.from_numpy(omega_host).to(device="cuda", dtype=cdt)
+    big = w.n * w.k * w.n_omega > (1 << 29)
+    if big:   # draw per frequency row straight into a pinned host block (no full complex128 copy)
+        pinned = torch.empty((w.n_omega, w.k, w.n), dtype=torch.complex64, pin_memory=True)
+        for j in range(w.n_omega):
+            pinned[j].copy_(torch.from_numpy(W.test_block_row(w, j, seed_offset=rank_seed_offset(rank))))
+        omega_dev = pinned.to(device="cuda", dtype=cdt)
+    else:
+        omega_host = W.test_block(w, seed_offset=rank_seed_offset(rank))
+        omega_dev = torch.from_numpy(omega_host).to(device="cuda", dtype=cdt)
+        pinned = torch.from_numpy(omega_host.astype(np.complex128 if prec_name == "fp64" else np.complex64)).pin_memory()
     ninst = n_instances(w)
     gains = np.zeros((ninst, w.n_omega, w.n_modes))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -331,7 +357,6 @@ def run_ours(args):
     gains_timed = gains.copy()
 
     # end to end through the public API: pinned host test block in, gains on the host out
-    pinned = torch.from_numpy(omega_host.astype(np.complex128 if prec_name == "fp64" else np.complex64)).pin_memory()
     h2d = pinned.numel() * pinned.element_size()
     d2h = gains.nbytes
     e2e_ms = 0.0

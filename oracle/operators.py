@@ -2,7 +2,7 @@
 
 Each builder writes the discretised operator of Sec. 2.1 Eq. (system) (here in
 the form du/dt = A u + f) as a scipy sparse matrix, straight from the
-difference formulas, one stencil entry at a time.  The adjoint system of
+difference formulas: one array of entries per stencil direction.  The adjoint system of
 Sec. 2.1 Eq. (adsystem) with identity metrics uses A^H (discrete adjoints with W = I).
 """
 from __future__ import annotations
@@ -58,25 +58,32 @@ def adr2d_fields(sysm):
     return dx, dy, u, react, sigma
 
 
+def _couple(rows, cols, vals, p, q, v, mask):
+    rows.append(p[mask]); cols.append(q[mask]); vals.append(np.broadcast_to(v, p.shape)[mask])
+
+
 def adr2d(sysm) -> sps.csr_matrix:
-    """2-D ADR: -U(y) u_x + visc lap(u) + (r(y) - sigma) u, index p = iy * nx + ix."""
+    """2-D ADR: -U(y) u_x + visc lap(u) + (r(y) - sigma) u, index p = iy * nx + ix.
+
+    Entries (central differences, Dirichlet zeros outside the grid):
+      diagonal  -2 visc/dx^2 - 2 visc/dy^2 + r(y) - sigma(x, y)
+      (ix -/+ 1)  +/- U(y)/(2 dx) + visc/dx^2,   (iy -/+ 1)  visc/dy^2.
+    """
     dx, dy, u, react, sigma = adr2d_fields(sysm)
     nx, ny, nu = sysm.nx, sysm.ny, sysm.visc
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    p = (jj * nx + ii).ravel()
+    jf, i_f = jj.ravel(), ii.ravel()
+    uy = u[jf]
     rows, cols, vals = [], [], []
-    for j in range(ny):
-        for i in range(nx):
-            p = j * nx + i
-            rows.append(p); cols.append(p)
-            vals.append(-2.0 * nu / dx ** 2 - 2.0 * nu / dy ** 2 + react[j] - sigma[j, i])
-            if i > 0:
-                rows.append(p); cols.append(p - 1); vals.append(u[j] / (2 * dx) + nu / dx ** 2)
-            if i < nx - 1:
-                rows.append(p); cols.append(p + 1); vals.append(-u[j] / (2 * dx) + nu / dx ** 2)
-            if j > 0:
-                rows.append(p); cols.append(p - nx); vals.append(nu / dy ** 2)
-            if j < ny - 1:
-                rows.append(p); cols.append(p + nx); vals.append(nu / dy ** 2)
-    return sps.csr_matrix((np.array(vals), (rows, cols)), shape=(nx * ny, nx * ny))
+    _couple(rows, cols, vals, p, p, -2.0 * nu / dx ** 2 - 2.0 * nu / dy ** 2 + react[jf] - sigma.ravel(),
+            np.ones_like(p, bool))
+    _couple(rows, cols, vals, p, p - 1, uy / (2 * dx) + nu / dx ** 2, i_f > 0)
+    _couple(rows, cols, vals, p, p + 1, -uy / (2 * dx) + nu / dx ** 2, i_f < nx - 1)
+    _couple(rows, cols, vals, p, p - nx, nu / dy ** 2, jf > 0)
+    _couple(rows, cols, vals, p, p + nx, nu / dy ** 2, jf < ny - 1)
+    return sps.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(nx * ny, nx * ny))
 
 
 def adv3d_fields(sysm):
@@ -103,39 +110,35 @@ def adv3d_fields(sysm):
 def adv3d(sysm) -> sps.csr_matrix:
     """3-D, 3 components: -(U.grad)u_c + visc lap(u_c) - delta_{c,x} (u.grad)U_x.
 
-    Index p = ((c * nz + kz) * ny + jy) * nx + ix.
+    Index p = ((c * nz + kz) * ny + jy) * nx + ix.  Entries per component c:
+      diagonal  -2 visc (1/dx^2 + 1/dy^2 + 1/dz^2),
+      (ix -/+ 1)  +/- U(x,y,z)/(2 dx) + visc/dx^2,  (jy -/+ 1) visc/dy^2,  (kz -/+ 1) visc/dz^2;
+    component x also couples to every component cc at the same cell with -dU_x/dx_cc.
     """
     (dx, dy, dz), ux, dudx, dudy, dudz = adv3d_fields(sysm)
     nx, ny, nz, nu = sysm.nx, sysm.ny, sysm.nz, sysm.visc
     ncell = nx * ny * nz
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cell = ((kk * ny + jj) * nx + ii).ravel()
+    i_f, j_f, k_f = ii.ravel(), jj.ravel(), kk.ravel()
+    u = ux.ravel()
+    grads = (dudx.ravel(), dudy.ravel(), dudz.ravel())
+    diag = -2.0 * nu * (1 / dx ** 2 + 1 / dy ** 2 + 1 / dz ** 2)
     rows, cols, vals = [], [], []
-    grads = (dudx, dudy, dudz)
+    allm = np.ones_like(cell, bool)
     for c in range(3):
-        for kz in range(nz):
-            for jy in range(ny):
-                for ix in range(nx):
-                    cell = (kz * ny + jy) * nx + ix
-                    p = c * ncell + cell
-                    u = ux[kz, jy, ix]
-                    diag = -2.0 * nu * (1 / dx ** 2 + 1 / dy ** 2 + 1 / dz ** 2)
-                    rows.append(p); cols.append(p); vals.append(diag)
-                    if ix > 0:
-                        rows.append(p); cols.append(p - 1); vals.append(u / (2 * dx) + nu / dx ** 2)
-                    if ix < nx - 1:
-                        rows.append(p); cols.append(p + 1); vals.append(-u / (2 * dx) + nu / dx ** 2)
-                    if jy > 0:
-                        rows.append(p); cols.append(p - nx); vals.append(nu / dy ** 2)
-                    if jy < ny - 1:
-                        rows.append(p); cols.append(p + nx); vals.append(nu / dy ** 2)
-                    if kz > 0:
-                        rows.append(p); cols.append(p - nx * ny); vals.append(nu / dz ** 2)
-                    if kz < nz - 1:
-                        rows.append(p); cols.append(p + nx * ny); vals.append(nu / dz ** 2)
-                    if c == 0:
-                        for cc in range(3):
-                            rows.append(p); cols.append(cc * ncell + cell)
-                            vals.append(-grads[cc][kz, jy, ix])
-    return sps.csr_matrix((np.array(vals), (rows, cols)), shape=(3 * ncell, 3 * ncell))
+        p = c * ncell + cell
+        _couple(rows, cols, vals, p, p, np.full(p.shape, diag), allm)
+        _couple(rows, cols, vals, p, p - 1, u / (2 * dx) + nu / dx ** 2, i_f > 0)
+        _couple(rows, cols, vals, p, p + 1, -u / (2 * dx) + nu / dx ** 2, i_f < nx - 1)
+        _couple(rows, cols, vals, p, p - nx, np.full(p.shape, nu / dy ** 2), j_f > 0)
+        _couple(rows, cols, vals, p, p + nx, np.full(p.shape, nu / dy ** 2), j_f < ny - 1)
+        _couple(rows, cols, vals, p, p - nx * ny, np.full(p.shape, nu / dz ** 2), k_f > 0)
+        _couple(rows, cols, vals, p, p + nx * ny, np.full(p.shape, nu / dz ** 2), k_f < nz - 1)
+    for cc in range(3):
+        _couple(rows, cols, vals, cell, cc * ncell + cell, -grads[cc], allm)
+    return sps.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(3 * ncell, 3 * ncell))
 
 
 def dense(a) -> np.ndarray:

@@ -233,6 +233,22 @@ def test_block(w: Workload, k: int | None = None, seed_offset: int = 0) -> np.nd
     return gaussian_block(w.seed + seed_offset, w.n_omega, kk, w.n, real_rows)
 
 
+def test_block_row(w: Workload, j: int, k: int | None = None, seed_offset: int = 0) -> np.ndarray:
+    """Row j ([k][n], complex64) of a test block drawn one frequency at a time.
+
+    For blocks too large to draw at once on the host (tens of GB): each row has
+    its own stream, numpy.random.default_rng((seed, j)); same distribution as
+    `gaussian_block` (not the same numbers).
+    """
+    kk = w.k if k is None else k
+    rng = np.random.default_rng((w.seed + seed_offset, j))
+    re = rng.standard_normal((kk, w.n), dtype=np.float32)
+    if w.real_state and w.omegas[j] == 0.0:
+        return re.astype(np.complex64)
+    im = rng.standard_normal((kk, w.n), dtype=np.float32)
+    return ((re + 1j * im) / np.float32(math.sqrt(2.0))).astype(np.complex64)
+
+
 def hermite_gl_matrix(sysm: Dense) -> np.ndarray:
     """Dense GL operator on Hermite-function collocation nodes (input data).
 
