@@ -180,35 +180,41 @@ __global__ void __launch_bounds__(256, 1) dense_tc_step_kernel(TcStepArgs a) {
 // MB * CS CTAs, one per SM, all resident at once.  CTA (mb, j) keeps the A
 // tile of row block mb and K slice j in shared memory for the whole tile.
 //
-// The test vectors are split into up to four independent chains of 8
-// vectors (MMA N = 16: 8 real + 8 imaginary columns).  Each chain is driven
-// by its own four warps with its own operand buffers, mbarriers, tensor-memory
-// columns, accumulators and step counters, so while one chain waits on its
-// hand-off latency the tensor core works on another.  Per chain and step a
-// CTA waits until row blocks 2j and 2j+1 (the producers of its K slice) have
-// published the step, bulk-copies its X slice, runs the MMAs, and adds its
-// 128 x 16 partial into the row block's FP32 accumulator with vector atomics
-// in L2.  The last CTA of the row block to arrive (arrival counter) does the
-// RK4 epilogue for the block's 64 rows, re-zeroes the accumulator and
-// publishes the chain's step counter for the block.  Every row block reads
-// all K slices, so no CTA runs more than one step ahead of any other within
-// a chain: accumulators, counters and X operands are double-buffered by step
-// parity.  Spins are bounded and stop early once any CTA has set the error.
+// The test vectors are split into up to two independent chains of 16 vectors
+// (32 real columns), each driven by its own four warps with its own operand
+// buffer, mbarriers, tensor-memory columns and counters, so one chain's
+// hand-off latency overlaps the other chain's work.  Per chain and step:
+//   1. wait until row blocks 2j and 2j+1 have published the state (counter),
+//      bulk-copy the TF32 hi / lo split of the state slice (32 KB);
+//   2. two MMAs per K-step: A_hi x [X_hi | X_lo] (N = 64) and A_lo x X_hi
+//      (N = 32), so the A tile is read from shared memory twice, not three times;
+//   3. sum the three product groups out of tensor memory into the CTA's
+//      128 x 32 partial, store it (L2) and count it in the row block's counter;
+//   4. as owner of 64/CS rows of its row block, wait for all CS partials of the
+//      step, sum them, apply the RK4 update u <- u + D u + F (the owner keeps
+//      its rows of u in registers for the whole tile), write the snapshot and
+//      the hi / lo split of the new state, and count the publication.
+// Partials, split states and counter targets are double-buffered by step
+// parity: every row block reads every K slice, so no CTA runs more than one
+// step ahead of any other within a chain.  Counters only grow (zeroed at the
+// start of a march).  Spins are bounded in time and stop once any CTA has set
+// the error flag.
 // ---------------------------------------------------------------------------
-constexpr int kChainVec = 8;                         // vectors per chain
-constexpr int kChainN = 2 * kChainVec;               // MMA N per chain
-constexpr int kMaxChains = 4;
-constexpr uint32_t kXcFloats = kChainN * kTileK;     // 2048 floats = 8 KB per hi / lo
-constexpr uint32_t kSmemPersistent = 4 * (2 * kATileFloats + kMaxChains * 2 * kXcFloats) + 256;
-constexpr uint32_t kSpinTries = 1u << 24;
+constexpr int kChainVec = 16;                        // vectors per chain
+constexpr int kChainN = 2 * kChainVec;               // real columns per chain (re, im)
+constexpr int kMaxChains = 2;
+constexpr uint32_t kXcFloats = 2 * kChainN * kTileK; // hi rows [0, 32) then lo rows [32, 64): 8192 floats
+constexpr uint32_t kPartFloats = kM * kChainN;       // 128 x 32 partial of one CTA
+constexpr uint32_t kSmemPersistent = 4 * (2 * kATileFloats + kMaxChains * kXcFloats) + 256;
+constexpr int kMarchThreads = 128 * kMaxChains;
 
 struct TcMarchArgs {
   const float* A;
-  float* X;                 // [chains][2][CS][2][kXcFloats]
-  float* acc;               // [chains][2][MB][kM][kChainN]
-  int* cnt;                 // [chains][2][MB]
-  int* ready;               // [chains][MB]
-  cpx<float>* u;            // [2][kg][n]
+  float* X;                 // [chains][2][CS][kXcFloats]
+  float* part;              // [chains][2][MB][CS][kPartFloats]
+  int* cnt;                 // [chains][2][MB]  partials stored
+  int* ready;               // [chains][MB]     owner publications
+  cpx<float>* u;            // [2][kg][n]: state at n0 in slot n0 & 1, written back to slot (n0 + steps) & 1
   const cpx<float>* F;      // [steps][kg][n] or null
   cpx<float>* Y;            // [steps][kg][n] or null
   int64_t n0;
@@ -223,14 +229,13 @@ __device__ __forceinline__ void chain_bar(int chain) {
   asm volatile("bar.sync %0, 128;" ::"r"(1 + chain) : "memory");
 }
 
-__global__ void __launch_bounds__(512, 1) dense_tc_march_kernel(TcMarchArgs a) {
+__global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarchArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   float* A_hi = reinterpret_cast<float*>(smem);
   float* A_lo = A_hi + kATileFloats;
-  float* Xs = A_lo + kATileFloats;                                         // [chain][hi, lo][kXcFloats]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Xs + kMaxChains * 2 * kXcFloats);  // [0] A, then 2 per chain
+  float* Xs = A_lo + kATileFloats;                                          // [chain][kXcFloats]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Xs + kMaxChains * kXcFloats);  // [0] A, then 2 per chain
   uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 1 + 2 * kMaxChains);
-  int* last = reinterpret_cast<int*>(tbase + 1);                          // [chain]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int chain = warp >> 2;                  // warps 4c .. 4c + 3 drive chain c
@@ -238,11 +243,12 @@ __global__ void __launch_bounds__(512, 1) dense_tc_march_kernel(TcMarchArgs a) {
   const int MB = a.n / kTileRows;
   const int mb = blockIdx.x / a.cs;
   const int j = blockIdx.x % a.cs;
+  const volatile int* errv = a.err;
   if (tid == 0) {
     for (int b = 0; b < 1 + 2 * kMaxChains; ++b) tc::mbar_init(&bars[b], 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(tbase, 64);
+  if (warp == 0) tc::tmem_alloc(tbase, 256);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -253,140 +259,190 @@ __global__ void __launch_bounds__(512, 1) dense_tc_march_kernel(TcMarchArgs a) {
     tc::bulk_g2s(A_hi, at, 4 * kATileFloats, &bars[0]);
     tc::bulk_g2s(A_lo, at + kATileFloats, 4 * kATileFloats, &bars[0]);
   }
-  bool ok = tc::mbar_wait(&bars[0], 0, kWaitTries);
+  bool ok = tc::mbar_wait(&bars[0], 0, 0xFFFFFFFFu, errv);
   __syncthreads();
   if (chain < a.chains) {
-    float* X_hi = Xs + (size_t)chain * 2 * kXcFloats;
-    float* X_lo = X_hi + kXcFloats;
+    float* X_sm = Xs + (size_t)chain * kXcFloats;
     uint64_t* bar_x = &bars[1 + 2 * chain];
     uint64_t* bar_m = &bars[2 + 2 * chain];
-    const uint32_t tcol = tmem + (uint32_t)(chain * kChainN);
-    const size_t xset = (size_t)a.cs * 2 * kXcFloats;
+    const uint32_t tcol = tmem + (uint32_t)(chain * 128);
+    const size_t xset = (size_t)a.cs * kXcFloats;                // one parity
     float* Xg = a.X + (size_t)chain * 2 * xset;
-    float* accg = a.acc + (size_t)chain * 2 * MB * kM * kChainN;
+    float* partg = a.part + (size_t)chain * 2 * MB * a.cs * kPartFloats;
     int* cnt = a.cnt + chain * 2 * MB;
     int* ready = a.ready + chain * MB;
     const int64_t rows = (int64_t)a.kg * a.n;
-    const int v0 = chain * kChainVec;           // first vector of the chain
-    const uint32_t idesc = tc::idesc_tf32(kM, kChainN);
+    const int v0 = chain * kChainVec;
+    const uint32_t idesc_hx = tc::idesc_tf32(kM, 2 * kChainN);   // A_hi x [X_hi | X_lo]
+    const uint32_t idesc_lx = tc::idesc_tf32(kM, kChainN);       // A_lo x X_hi
     const uint32_t sbo = (kTileK / 4) * 128;
-    volatile int* errv = a.err;
+    // owner pairs: rows [rpc j, rpc j + rpc) of the row block x 16 vectors, kPairs per thread
+    const int rpc = kTileRows / a.cs;
+    const int npairs = rpc * kChainVec;
+    constexpr int kMaxPairs = kTileRows * kChainVec / 128;       // 8 (cs = 1)
+    const int vl = ctid & 15;
+    const int vg = v0 + vl;
+    cpx<float> u_own[kMaxPairs];
+#pragma unroll
+    for (int q = 0; q < kMaxPairs; ++q) {
+      const int pidx = ctid + 128 * q;
+      const int i = mb * kTileRows + rpc * j + (pidx >> 4);
+      u_own[q] = (pidx < npairs && vg < a.kg) ? a.u[(size_t)(a.n0 & 1) * rows + (int64_t)vg * a.n + i]
+                                               : mk<float>(0.f, 0.f);
+    }
+    // X slot layout: hi rows [0, 32) (re of 16 vectors, then im), lo rows [32, 64)
+    auto write_x = [&](float* xo_par, int i, cpx<float> u1) {
+      const int js = i / kTileK, kk = i % kTileK;
+      float* xo = xo_par + (size_t)js * kXcFloats;
+      const float hr = tc::to_tf32(u1.re), hi = tc::to_tf32(u1.im);
+      __stcg(xo + tc::kmajor_offset(vl, kk, kTileK) / 4, hr);
+      __stcg(xo + tc::kmajor_offset(kChainVec + vl, kk, kTileK) / 4, hi);
+      __stcg(xo + tc::kmajor_offset(kChainN + vl, kk, kTileK) / 4, u1.re - hr);
+      __stcg(xo + tc::kmajor_offset(kChainN + kChainVec + vl, kk, kTileK) / 4, u1.im - hi);
+    };
+    if (a.n0 == 0) {  // publish the initial state's split (later tiles find it from the previous tile)
+#pragma unroll
+      for (int q = 0; q < kMaxPairs; ++q) {
+        const int pidx = ctid + 128 * q;
+        if (pidx < npairs) write_x(Xg, mb * kTileRows + rpc * j + (pidx >> 4), u_own[q]);
+      }
+      chain_bar(chain);
+      if (ctid == 0) tc::red_release_add(&ready[mb], 1);
+    }
+    // Every thread of the chain runs every step (named barriers need all 128);
+    // after an error the waits return at once and the flag reports the failure.
     for (int s = 0; s < a.steps; ++s) {
       const int64_t n = a.n0 + s;
       const int par = (int)(n & 1);
-      if (ctid == 0) {
-        bool got = false;
-        for (uint32_t it = 0; it < kSpinTries; ++it) {
-          if (*errv != 0) break;
-          if (tc::ld_acquire(&ready[2 * j]) >= (int)n && tc::ld_acquire(&ready[2 * j + 1]) >= (int)n) {
-            got = true;
-            break;
-          }
-        }
-        if (!got) atomicExch(a.err, 2);
-        tc::fence_proxy_async_global();
-        const float* xt = Xg + (size_t)par * xset + (size_t)j * 2 * kXcFloats;
-        tc::mbar_arrive_expect_tx(bar_x, 4 * 2 * kXcFloats);
-        tc::bulk_g2s(X_hi, xt, 4 * kXcFloats, bar_x);
-        tc::bulk_g2s(X_lo, xt + kXcFloats, 4 * kXcFloats, bar_x);
+      // forcing of this step for the owned pairs: loads in flight during the MMA phase
+      const cpx<float>* Fs = (a.F != nullptr && n < a.n_forced) ? a.F + (size_t)s * rows : nullptr;
+      cpx<float> fv[kMaxPairs];
+#pragma unroll
+      for (int q = 0; q < kMaxPairs; ++q) {
+        const int pidx = ctid + 128 * q;
+        const int i = mb * kTileRows + rpc * j + (pidx >> 4);
+        fv[q] = (Fs != nullptr && pidx < npairs && vg < a.kg)
+                    ? mk<float>(__ldcs(reinterpret_cast<const float*>(Fs + (int64_t)vg * a.n + i)),
+                                __ldcs(reinterpret_cast<const float*>(Fs + (int64_t)vg * a.n + i) + 1))
+                    : mk<float>(0.f, 0.f);
       }
-      ok = tc::mbar_wait(bar_x, (uint32_t)(s & 1), kWaitTries) && ok;
-      tc::tc_fence_after();
+      // 1. the state slice of this step
       if (ctid == 0) {
-        if (ok) {
-#pragma unroll 1
+        const int target = a.cs * (int)(n + 1);
+        const bool got = tc::spin_until_geq(&ready[2 * j], target, errv) &&
+                         tc::spin_until_geq(&ready[2 * j + 1], target, errv);
+        if (!got) {
+          atomicExch(a.err, 2);
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar_x)) : "memory");
+        } else {
+          tc::fence_proxy_async_global();
+          tc::mbar_arrive_expect_tx(bar_x, 4 * kXcFloats);
+          tc::bulk_g2s(X_sm, Xg + (size_t)par * xset + (size_t)j * kXcFloats, 4 * kXcFloats, bar_x);
+        }
+      }
+      // 2. products
+      if (ctid == 0) {
+        bool okx = tc::mbar_wait(bar_x, (uint32_t)(s & 1), 0xFFFFFFFFu, errv) && *errv == 0;
+        tc::tc_fence_after();
+        if (okx) {
+#pragma unroll 4
           for (int ks = 0; ks < kTileK / 8; ++ks) {
             const uint64_t ah = tc::smem_desc(reinterpret_cast<char*>(A_hi) + ks * 256, 128, sbo);
             const uint64_t al = tc::smem_desc(reinterpret_cast<char*>(A_lo) + ks * 256, 128, sbo);
-            const uint64_t xh = tc::smem_desc(reinterpret_cast<char*>(X_hi) + ks * 256, 128, sbo);
-            const uint64_t xl = tc::smem_desc(reinterpret_cast<char*>(X_lo) + ks * 256, 128, sbo);
-            tc::mma_tf32(tcol, ah, xh, idesc, ks > 0);
-            tc::mma_tf32(tcol, ah, xl, idesc, true);
-            tc::mma_tf32(tcol, al, xh, idesc, true);
+            const uint64_t xx = tc::smem_desc(reinterpret_cast<char*>(X_sm) + ks * 256, 128, sbo);
+            tc::mma_tf32(tcol, ah, xx, idesc_hx, ks > 0);
+            tc::mma_tf32(tcol + 2 * kChainN, al, xx, idesc_lx, ks > 0);
           }
           tc::mma_commit(bar_m);
         } else {
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar_m)) : "memory");
         }
       }
-      ok = tc::mbar_wait(bar_m, (uint32_t)(s & 1), kWaitTries) && ok;
+      ok = tc::mbar_wait(bar_m, (uint32_t)(s & 1), 0xFFFFFFFFu, errv) && ok && *errv == 0;
       tc::tc_fence_after();
-      float* accb = accg + ((size_t)par * MB + mb) * kM * kChainN;
-      if (ok) {
-        const int qw = warp & 3;                 // TMEM lane quadrant of this warp
+      // 3. partial: hi*hi + hi*lo + lo*hi, one row per thread
+      float* pb = partg + (((size_t)par * MB + mb) * a.cs + j) * kPartFloats;
+      {
+        const int qw = warp & 3;
         const int row = 32 * qw + lane;
-        float v[16];
-        tc::tmem_ld16(tcol + ((uint32_t)(32 * qw) << 16), v);
-        float4* dst = reinterpret_cast<float4*>(accb + row * kChainN);
+        const uint32_t tl = tcol + ((uint32_t)(32 * qw) << 16);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        for (int h = 0; h < 2; ++h) {
+          float x0[16], x1[16], x2[16];
+          tc::tmem_ld16(tl + 16 * h, x0);
+          tc::tmem_ld16(tl + kChainN + 16 * h, x1);
+          tc::tmem_ld16(tl + 2 * kChainN + 16 * h, x2);
+          float4* dst = reinterpret_cast<float4*>(pb + row * kChainN + 16 * h);
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            __stcg(dst + c, make_float4(x0[4 * c] + x1[4 * c] + x2[4 * c], x0[4 * c + 1] + x1[4 * c + 1] + x2[4 * c + 1],
+                                        x0[4 * c + 2] + x1[4 * c + 2] + x2[4 * c + 2],
+                                        x0[4 * c + 3] + x1[4 * c + 3] + x2[4 * c + 3]));
+        }
       }
-      __threadfence();
       tc::tc_fence_before();
       chain_bar(chain);
-      if (ctid == 0) last[chain] = (atomicAdd(&cnt[par * MB + mb], 1) == a.cs - 1);
+      if (ctid == 0) tc::red_release_add(&cnt[par * MB + mb], 1);
+      // 4. owner: all partials of the row block for this step
+      if (ctid == 0) {
+        if (!tc::spin_until_geq(&cnt[par * MB + mb], a.cs * (int)((n >> 1) + 1), errv)) atomicExch(a.err, 2);
+      }
       chain_bar(chain);
-      if (last[chain]) {
-        __threadfence();
-        const cpx<float>* uin = a.u + (size_t)par * rows;
-        cpx<float>* uout = a.u + (size_t)(1 - par) * rows;
-        const cpx<float>* Fs = (a.F != nullptr && n < a.n_forced) ? a.F + (size_t)s * rows : nullptr;
-        cpx<float>* Ys = (a.Y != nullptr && s >= a.y_first) ? a.Y + (size_t)s * rows : nullptr;
-        float* xout = Xg + (size_t)(1 - par) * xset;
-        // 64 rows x 8 vectors = 512 (row, vector) pairs, 4 per thread; all loads issued first
-        constexpr int kPairs = kTileRows * kChainVec / 128;
-        const int vl = ctid & 7;
-        const int vg = v0 + vl;
-        float prr[kPairs], pri[kPairs], pir[kPairs], pii[kPairs];
-        float2 u0[kPairs], fv[kPairs];
+      ok = ok && *errv == 0;
+      cpx<float>* Ys = (a.Y != nullptr && s >= a.y_first) ? a.Y + (size_t)s * rows : nullptr;
+      float* xo_par = Xg + (size_t)(1 - par) * xset;
+      const float* pbase = partg + ((size_t)par * MB + mb) * a.cs * kPartFloats;
 #pragma unroll
-        for (int q = 0; q < kPairs; ++q) {
-          const int iloc = (ctid >> 3) + 16 * q;
-          prr[q] = __ldcg(accb + iloc * kChainN + vl);
-          pri[q] = __ldcg(accb + iloc * kChainN + kChainVec + vl);
-          pir[q] = __ldcg(accb + (64 + iloc) * kChainN + vl);
-          pii[q] = __ldcg(accb + (64 + iloc) * kChainN + kChainVec + vl);
-          const int64_t e = (int64_t)vg * a.n + mb * kTileRows + iloc;
-          u0[q] = vg < a.kg ? __ldcg(reinterpret_cast<const float2*>(uin + e)) : make_float2(0.f, 0.f);
-          fv[q] = (Fs && vg < a.kg) ? __ldcg(reinterpret_cast<const float2*>(Fs + e)) : make_float2(0.f, 0.f);
-        }
+      for (int q = 0; q < kMaxPairs; ++q) {
+        const int pidx = ctid + 128 * q;
+        if (pidx < npairs) {
+          const int iloc = rpc * j + (pidx >> 4);
+          float prr = 0.f, pri = 0.f, pir = 0.f, pii = 0.f;
+          float t0[8], t1[8], t2[8], t3[8];
 #pragma unroll
-        for (int q = 0; q < kPairs; ++q) {
-          const int iloc = (ctid >> 3) + 16 * q;
-          const int i = mb * kTileRows + iloc;
-          if (vg < a.kg && i < a.n) {
-            const int64_t e = (int64_t)vg * a.n + i;
-            const float2 u1 = make_float2(u0[q].x + (prr[q] - pii[q]) + fv[q].x, u0[q].y + (pri[q] + pir[q]) + fv[q].y);
-            __stcg(reinterpret_cast<float2*>(uout + e), u1);
-            if (Ys) __stcg(reinterpret_cast<float2*>(Ys + e), u0[q]);
-            const int js = i / kTileK, kk = i % kTileK;
-            float* xo = xout + (size_t)js * 2 * kXcFloats;
-            const float hr = tc::to_tf32(u1.x), hi = tc::to_tf32(u1.y);
-            const uint32_t o_re = tc::kmajor_offset(vl, kk, kTileK) / 4;
-            const uint32_t o_im = tc::kmajor_offset(kChainVec + vl, kk, kTileK) / 4;
-            __stcg(xo + o_re, hr);
-            __stcg(xo + kXcFloats + o_re, u1.x - hr);
-            __stcg(xo + o_im, hi);
-            __stcg(xo + kXcFloats + o_im, u1.y - hi);
+          for (int p = 0; p < 8; ++p) {
+            if (p < a.cs) {
+              const float* pp = pbase + (size_t)p * kPartFloats;
+              t0[p] = __ldcg(pp + iloc * kChainN + vl);
+              t1[p] = __ldcg(pp + iloc * kChainN + kChainVec + vl);
+              t2[p] = __ldcg(pp + (64 + iloc) * kChainN + vl);
+              t3[p] = __ldcg(pp + (64 + iloc) * kChainN + kChainVec + vl);
+            }
           }
-        }
-        chain_bar(chain);
-        for (int e = ctid; e < kM * kChainN / 4; e += 128)
-          __stcg(reinterpret_cast<float4*>(accb) + e, make_float4(0.f, 0.f, 0.f, 0.f));
-        tc::fence_proxy_async_global();
-        __threadfence();
-        chain_bar(chain);
-        if (ctid == 0) {
-          cnt[par * MB + mb] = 0;
-          tc::st_release(&ready[mb], (int)(n + 1));
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            if (p < a.cs) {
+              prr += t0[p];
+              pri += t1[p];
+              pir += t2[p];
+              pii += t3[p];
+            }
+          }
+          const int i = mb * kTileRows + iloc;
+          const cpx<float> u0 = u_own[q];
+          cpx<float> u1 = mk<float>(u0.re + (prr - pii) + fv[q].re, u0.im + (pri + pir) + fv[q].im);
+          if (vg >= a.kg) u1 = mk<float>(0.f, 0.f);
+          if (Ys != nullptr && vg < a.kg) __stcs(reinterpret_cast<float2*>(Ys + (int64_t)vg * a.n + i), make_float2(u0.re, u0.im));
+          write_x(xo_par, i, u1);
+          u_own[q] = u1;
         }
       }
+      chain_bar(chain);
+      if (ctid == 0) tc::red_release_add(&ready[mb], 1);
+    }
+    // state at the end of the tile
+    const int64_t nend = a.n0 + a.steps;
+#pragma unroll
+    for (int q = 0; q < kMaxPairs; ++q) {
+      const int pidx = ctid + 128 * q;
+      const int i = mb * kTileRows + rpc * j + (pidx >> 4);
+      if (pidx < npairs && vg < a.kg) a.u[(size_t)(nend & 1) * rows + (int64_t)vg * a.n + i] = u_own[q];
     }
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
   if (!ok && (tid & 127) == 0) atomicExch(a.err, 2);
 }
 
@@ -454,12 +510,12 @@ rsv_status dense_tc_prepare(rsv_operator op, const void* d64_direct) {
   if (!op->d_ready) {
     e = cudaMalloc(&op->d_ready, sizeof(int) * kMaxChains * 3 * MB);
     if (e == cudaSuccess) op->dev.push_back(op->d_ready);
-    if (e == cudaSuccess) e = cudaMalloc(&op->tc_acc, sizeof(float) * kMaxChains * 2 * MB * kM * kChainN);
+    if (e == cudaSuccess) e = cudaMalloc(&op->tc_acc, sizeof(float) * kMaxChains * 2 * MB * cs * kPartFloats);
     if (e == cudaSuccess) op->dev.push_back(op->tc_acc);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core march buffers");
   }
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_tc_march_kernel, 512, kSmemPersistent);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_tc_march_kernel, kMarchThreads, kSmemPersistent);
   if (e != cudaSuccess) {
     cudaGetLastError();
     per_sm = 0;
@@ -472,7 +528,7 @@ rsv_status dense_tc_prepare(rsv_operator op, const void* d64_direct) {
 
 // Operand buffers of the persistent kernel (per chain, two step parities).
 size_t dense_tc_chain_x_bytes(rsv_operator op) {
-  return (size_t)kMaxChains * 2 * (op->n / kTileK) * 2 * kXcFloats * sizeof(float);
+  return (size_t)kMaxChains * 2 * (op->n / kTileK) * kXcFloats * sizeof(float);
 }
 
 // A whole tile of steps in one persistent launch (requires op->tc_persistent).
@@ -484,9 +540,9 @@ cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n
   TcMarchArgs a;
   a.A = (const float*)op->tc_tiles[adjoint ? 1 : 0];
   a.X = (float*)xbuf;
-  a.acc = (float*)op->tc_acc;
-  a.ready = (int*)op->d_ready;
-  a.cnt = (int*)op->d_ready + kMaxChains * MB;
+  a.part = (float*)op->tc_acc;
+  a.cnt = (int*)op->d_ready;                       // [chains][2][MB]
+  a.ready = (int*)op->d_ready + kMaxChains * 2 * MB;  // [chains][MB]
   a.u = (cpx<float>*)state;
   a.F = (const cpx<float>*)F;
   a.Y = (cpx<float>*)Y;
@@ -502,11 +558,9 @@ cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n
   cudaError_t e = cudaSuccess;
   if (n0 == 0) {
     e = cudaMemsetAsync(op->d_ready, 0, sizeof(int) * kMaxChains * 3 * MB, op->stream);
-    if (e == cudaSuccess)
-      e = cudaMemsetAsync(op->tc_acc, 0, sizeof(float) * kMaxChains * 2 * MB * kM * kChainN, op->stream);
   }
   if (e != cudaSuccess) return e;
-  dense_tc_march_kernel<<<MB * cs, 512, kSmemPersistent, op->stream>>>(a);
+  dense_tc_march_kernel<<<MB * cs, kMarchThreads, kSmemPersistent, op->stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -114,7 +114,9 @@ cudaError_t gram_to_host(rsv_operator op, const void* X, int k, std::vector<cd>&
   cudaError_t e;
   {
     ProfScope ps(op, PROF_GLUE);
-    e = launch_gram<R>(X, op->n_omega, k, op->n, (const int64_t*)op->d_inst_off, op->n_inst,
+    int64_t max_len = 0;
+    for (int i = 0; i < op->n_inst; ++i) max_len = std::max(max_len, op->inst_len[i]);
+    e = launch_gram<R>(X, op->n_omega, k, op->n, (const int64_t*)op->d_inst_off, op->n_inst, max_len,
                        (cpx<double>*)op->ws_gram.ptr, op->stream);
   }
   if (e != cudaSuccess) return e;

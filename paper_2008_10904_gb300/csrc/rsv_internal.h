@@ -227,7 +227,7 @@ cudaError_t launch_gl1d_apply(const Gl1dTile& t, const int32_t* inst_of_point, c
 // G[j][i][a][b] = sum_{p in instance i} conj(X[j][a][p]) X[j][b][p]
 template <typename R>
 cudaError_t launch_gram(const void* X, int n_omega, int k, int64_t n, const int64_t* inst_off, int n_inst,
-                        cpx<double>* G, cudaStream_t st);
+                        int64_t max_len, cpx<double>* G, cudaStream_t st);
 // Out[j][b][p] = sum_a In[j][a][p] * M[j][inst(p)][a][b] * colscale[j][inst][b]
 template <typename R>
 cudaError_t launch_combine(const void* In, int n_omega, int ka, int kb, int64_t n, const int32_t* inst_of_point,

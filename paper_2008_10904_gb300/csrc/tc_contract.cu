@@ -252,6 +252,325 @@ __global__ void __launch_bounds__(256, 1) tc_contract_kernel(ContractArgs a) {
   if (!ok && tid == 0) atomicExch(a.err, 2);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined persistent variant (long operand streamed by bulk copies).
+//
+// One CTA per SM walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// with four warp roles connected by mbarrier rings:
+//   warp 8 (one thread)  producer: bulk-copies each K chunk of the long operand
+//                        in its storage precision into a 4-deep raw ring;
+//   warp 10 (one thread) producer: bulk-copies the chunk's pre-split twiddles
+//                        into a 2-deep B ring;
+//   warps 0-3            converters: one row each, raw value -> TF32 hi / lo in
+//                        the K-major operand layout (2 stages);
+//   warp 9 (one thread)  MMA issuer: 3 TF32 MMAs per K-step and N half into the
+//                        tile's tensor-memory accumulator, commits release the
+//                        operand stages and, after the last chunk, the tile;
+//   warps 4-7            epilogue: tensor memory -> F, or += FP64 accumulators;
+//                        then release the accumulator for the next tile.
+// The chunk sequence runs on across tiles, so the next tile's operands stream
+// in during the current tile's epilogue.  Every wait is bounded and also
+// returns once another role has aborted; on abort the producer and the MMA
+// issuer drain what they issued (bounded) before the CTA frees tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int kRawRing = 4;
+constexpr int kAStages = 2;
+constexpr int kBRing = 2;
+constexpr uint32_t kRawBytes = kRowsCta * kKc * 4;   // 128 rows x 16 real K values
+constexpr int kPipeThreads = 352;
+constexpr uint32_t kPipeSmem =
+    kRawRing * kRawBytes + kAStages * 2 * kAStageFloats * 4 + kBRing * 2 * kBStageFloats * 4 + 256;
+
+struct PipeBars {
+  uint64_t raw_full[kRawRing], raw_empty[kRawRing];
+  uint64_t a_full[kAStages], a_empty[kAStages];
+  uint64_t b_full[kBRing], b_empty[kBRing];
+  uint64_t acc_full, acc_empty;
+  int abort_flag;
+};
+
+__device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  return tc::mbar_wait(bar, parity, 0xFFFFFFFFu, abort_flag);
+}
+
+__device__ __forceinline__ void pabort(PipeBars* pb, int* err) {
+  *reinterpret_cast<volatile int*>(&pb->abort_flag) = 1;
+  atomicExch(err, 2);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// Raw layout of one chunk in shared memory: complex modes [8][128] float2
+// (pair index jj = frequency or step within the chunk), real analysis
+// [16][128] float.  Only the valid pair indices and rows are copied.
+__device__ __forceinline__ uint32_t issue_raw(const ContractArgs& a, int64_t r0, int nr, int kc, unsigned char* raw,
+                                              uint64_t* bar) {
+  const bool real = a.mode == ANAL_R;
+  const int npair = real ? kKc : kKc / 2;
+  const uint32_t esz = real ? 4 : 8;
+  int lo = kc * npair, hi = lo + npair;
+  if (a.mode == ANAL_C || a.mode == ANAL_R) {
+    lo = max(lo, a.s0);
+    hi = min(hi, a.s1);
+  } else {
+    hi = min(hi, a.n_omega);
+  }
+  const uint32_t bytes_row = (uint32_t)nr * esz;
+  const uint32_t total = hi > lo ? (uint32_t)(hi - lo) * bytes_row : 0u;
+  tc::mbar_arrive_expect_tx(bar, total);
+  const int64_t stride = (a.mode == ANAL_C || a.mode == ANAL_R) ? a.rows : a.src_stride;
+  for (int idx = lo; idx < hi; ++idx) {
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(a.src) + ((int64_t)idx * stride + r0) * esz;
+    tc::bulk_g2s(raw + (uint32_t)(idx - kc * npair) * kRowsCta * esz, src, bytes_row, bar);
+  }
+  return total;
+}
+
+__device__ __forceinline__ void convert_row(const ContractArgs& a, int64_t r0, int kc, int rr, const unsigned char* raw,
+                                            float* A_hi, float* A_lo) {
+  const bool row_ok = r0 + rr < a.rows;
+  float x[kKc];
+  if (a.mode == ANAL_R) {
+    const float* rv = reinterpret_cast<const float*>(raw);
+#pragma unroll
+    for (int kk = 0; kk < kKc; ++kk) {
+      const int s = kc * kKc + kk;
+      x[kk] = (row_ok && s >= a.s0 && s < a.s1) ? rv[kk * kRowsCta + rr] : 0.f;
+    }
+  } else {
+    const float2* rv = reinterpret_cast<const float2*>(raw);
+#pragma unroll
+    for (int jj = 0; jj < kKc / 2; ++jj) {
+      const int idx = kc * (kKc / 2) + jj;
+      const bool v = row_ok && ((a.mode == ANAL_C) ? (idx >= a.s0 && idx < a.s1) : (idx < a.n_omega));
+      const float2 c = v ? rv[jj * kRowsCta + rr] : make_float2(0.f, 0.f);
+      x[2 * jj] = c.x;
+      x[2 * jj + 1] = c.y;
+    }
+  }
+  // K-major core matrices: 4 consecutive K values of one row are one 16-byte vector
+#pragma unroll
+  for (int q = 0; q < kKc / 4; ++q) {
+    float4 h, l;
+    h.x = tc::to_tf32(x[4 * q]);
+    h.y = tc::to_tf32(x[4 * q + 1]);
+    h.z = tc::to_tf32(x[4 * q + 2]);
+    h.w = tc::to_tf32(x[4 * q + 3]);
+    l = make_float4(x[4 * q] - h.x, x[4 * q + 1] - h.y, x[4 * q + 2] - h.z, x[4 * q + 3] - h.w);
+    const uint32_t o = tc::kmajor_offset(rr, 4 * q, kKc) / 4;
+    *reinterpret_cast<float4*>(A_hi + o) = h;
+    *reinterpret_cast<float4*>(A_lo + o) = l;
+  }
+}
+
+__device__ __forceinline__ void epilogue_tile(const ContractArgs& a, int64_t r, uint32_t tq, bool ok) {
+  for (int c = 0; c < a.N; c += 16) {
+    float v[16];
+    tc::tmem_ld16(tq + (uint32_t)c, v);
+    if (!ok || r >= a.rows) continue;
+    if (a.mode == SYNTH_C) {
+      cpx<float>* F = reinterpret_cast<cpx<float>*>(a.out);
+#pragma unroll
+      for (int q = 0; q < 16; q += 2) {
+        const int tau = (c + q) >> 1;
+        if (tau < a.n_tau) __stcs(reinterpret_cast<float2*>(F + (int64_t)(a.tau0 + tau) * a.rows + r), make_float2(v[q], v[q + 1]));
+      }
+    } else if (a.mode == SYNTH_R) {
+      float* F = reinterpret_cast<float*>(a.out);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int tau = c + q;
+        if (tau < a.n_tau) __stcs(F + (int64_t)(a.tau0 + tau) * a.rows + r, v[q]);
+      }
+    } else {
+      cpx<double>* __restrict__ acc = reinterpret_cast<cpx<double>*>(a.out);
+      double2 old[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = (c >> 1) + q;
+        old[q] = j < a.n_omega ? __ldcs(reinterpret_cast<const double2*>(acc + (int64_t)j * a.acc_stride + r))
+                               : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = (c >> 1) + q;
+        if (j < a.n_omega)
+          __stcs(reinterpret_cast<double2*>(acc + (int64_t)j * a.acc_stride + r),
+                 make_double2(old[q].x + (double)v[2 * q], old[q].y + (double)v[2 * q + 1]));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(ContractArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* raw = smem;                                                     // [kRawRing][kRawBytes]
+  float* sA = reinterpret_cast<float*>(smem + kRawRing * kRawBytes);             // [kAStages][hi, lo][..]
+  float* sB = sA + kAStages * 2 * kAStageFloats;                                 // [kBRing][hi, lo][..]
+  PipeBars* pb = reinterpret_cast<PipeBars*>(sB + kBRing * 2 * kBStageFloats);
+  __shared__ uint32_t tbase;
+  volatile int* abort_flag = &pb->abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < kRawRing; ++i) {
+      tc::mbar_init(&pb->raw_full[i], 1);
+      tc::mbar_init(&pb->raw_empty[i], 128);
+    }
+    for (int i = 0; i < kAStages; ++i) {
+      tc::mbar_init(&pb->a_full[i], 128);
+      tc::mbar_init(&pb->a_empty[i], 1);
+    }
+    for (int i = 0; i < kBRing; ++i) {
+      tc::mbar_init(&pb->b_full[i], 1);
+      tc::mbar_init(&pb->b_empty[i], 1);
+    }
+    tc::mbar_init(&pb->acc_full, 1);
+    tc::mbar_init(&pb->acc_empty, 128);
+    pb->abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase, 512);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tbase;
+  const int chunks = a.K / kKc;
+  const int64_t tiles = (a.rows + kRowsCta - 1) / kRowsCta;
+  const uint32_t bchunk_bytes = 4u * (uint32_t)a.N * kKc;
+
+  if (warp == 8) {
+    if (lane == 0) {  // producer of the long operand
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int64_t r0 = t * kRowsCta;
+        const int nr = (int)min((int64_t)kRowsCta, a.rows - r0);
+        for (int kc = 0; kc < chunks; ++kc, ++g) {
+          const uint32_t rs = g % kRawRing, ru = g / kRawRing;
+          if (ru > 0 && !pwait(&pb->raw_empty[rs], (ru - 1) & 1, abort_flag)) { ok = false; break; }
+          issue_raw(a, r0, nr, kc, raw + rs * kRawBytes, &pb->raw_full[rs]);
+        }
+      }
+      if (!ok) {
+        pabort(pb, a.err);
+        for (uint32_t q = 0; q < kRawRing && q < g; ++q) {  // the last copies land on their full barriers
+          const uint32_t gg = g - 1 - q;
+          tc::mbar_wait(&pb->raw_full[gg % kRawRing], (gg / kRawRing) & 1, kTries);
+        }
+      }
+    }
+  } else if (warp == 10) {
+    if (lane == 0) {  // producer of the twiddle operand (the same chunks for every tile)
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        for (int kc = 0; kc < chunks; ++kc, ++g) {
+          const uint32_t bs = g % kBRing, bu = g / kBRing;
+          if (bu > 0 && !pwait(&pb->b_empty[bs], (bu - 1) & 1, abort_flag)) { ok = false; break; }
+          float* B_hi = sB + bs * 2 * kBStageFloats;
+          const float* bsrc = a.B + (size_t)kc * 2 * kBStageFloats;
+          tc::mbar_arrive_expect_tx(&pb->b_full[bs], 2 * bchunk_bytes);
+          tc::bulk_g2s(B_hi, bsrc, bchunk_bytes, &pb->b_full[bs]);
+          tc::bulk_g2s(B_hi + kBStageFloats, bsrc + kBStageFloats, bchunk_bytes, &pb->b_full[bs]);
+        }
+      }
+      if (!ok) {
+        pabort(pb, a.err);
+        for (uint32_t q = 0; q < kBRing && q < g; ++q) {
+          const uint32_t gg = g - 1 - q;
+          tc::mbar_wait(&pb->b_full[gg % kBRing], (gg / kBRing) & 1, kTries);
+        }
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {  // MMA issuer
+      uint32_t g = 0, tt = 0;
+      bool ok = true;
+      const uint32_t sbo = (kKc / 4) * 128;
+      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tt) {
+        if (tt > 0 && !pwait(&pb->acc_empty, (tt - 1) & 1, abort_flag)) { ok = false; break; }
+        tc::tc_fence_after();
+        for (int kc = 0; kc < chunks; ++kc, ++g) {
+          const uint32_t as = g % kAStages, au = g / kAStages;
+          const uint32_t bs = g % kBRing, bu = g / kBRing;
+          if (!pwait(&pb->a_full[as], au & 1, abort_flag) || !pwait(&pb->b_full[bs], bu & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const char* A_hi = reinterpret_cast<const char*>(sA + as * 2 * kAStageFloats);
+          const char* A_lo = A_hi + 4 * kAStageFloats;
+          const char* B_hi = reinterpret_cast<const char*>(sB + bs * 2 * kBStageFloats);
+          const char* B_lo = B_hi + 4 * kBStageFloats;
+#pragma unroll
+          for (int ks = 0; ks < kKc / 8; ++ks) {
+            const uint64_t ah = tc::smem_desc(A_hi + ks * 256, 128, sbo);
+            const uint64_t al = tc::smem_desc(A_lo + ks * 256, 128, sbo);
+            for (int nh = 0; nh < a.N; nh += 256) {
+              const int nn = min(256, a.N - nh);
+              const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)nn);
+              const uint64_t bh = tc::smem_desc(B_hi + ks * 256 + (nh / 8) * sbo, 128, sbo);
+              const uint64_t bl = tc::smem_desc(B_lo + ks * 256 + (nh / 8) * sbo, 128, sbo);
+              const uint32_t d = tmem + (uint32_t)nh;
+              tc::mma_tf32(d, ah, bh, idesc, kc > 0 || ks > 0);
+              tc::mma_tf32(d, ah, bl, idesc, true);
+              tc::mma_tf32(d, al, bh, idesc, true);
+            }
+          }
+          tc::mma_commit(&pb->a_empty[as]);
+          tc::mma_commit(&pb->b_empty[bs]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&pb->acc_full);
+      }
+      if (!ok) {
+        pabort(pb, a.err);
+        // every MMA issued so far completes before tensor memory is freed
+        tc::mma_commit(&pb->acc_full);
+        tc::mbar_wait(&pb->acc_full, tt & 1, kTries);
+      }
+    }
+  } else if (warp < 4) {  // converters: one row each
+    const int rr = tid;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      const int64_t r0 = t * kRowsCta;
+      for (int kc = 0; kc < chunks; ++kc, ++g) {
+        const uint32_t rs = g % kRawRing, ru = g / kRawRing;
+        const uint32_t as = g % kAStages, au = g / kAStages;
+        if (!pwait(&pb->raw_full[rs], ru & 1, abort_flag)) { ok = false; break; }
+        if (au > 0 && !pwait(&pb->a_empty[as], (au - 1) & 1, abort_flag)) { ok = false; break; }
+        float* A_hi = sA + as * 2 * kAStageFloats;
+        convert_row(a, r0, kc, rr, raw + rs * kRawBytes, A_hi, A_hi + kAStageFloats);
+        tc::fence_proxy_async_smem();
+        mbar_arrive(&pb->a_full[as]);
+        mbar_arrive(&pb->raw_empty[rs]);
+      }
+    }
+    if (!ok) pabort(pb, a.err);
+  } else if (warp >= 4 && warp < 8) {  // epilogue, TMEM lane quadrant warp % 4
+    const int q = warp & 3;
+    uint32_t tt = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tt) {
+      if (!pwait(&pb->acc_full, tt & 1, abort_flag)) { ok = false; break; }
+      tc::tc_fence_after();
+      epilogue_tile(a, t * kRowsCta + 32 * q + lane, tmem + ((uint32_t)(32 * q) << 16), true);
+      tc::tc_fence_before();
+      mbar_arrive(&pb->acc_empty);
+    }
+    if (!ok) pabort(pb, a.err);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
 // B operand of the tile: element (nrow, k) in chunk k / 16, TF32 hi / lo, K-major.
 __global__ void build_b_kernel(ContractArgs a, TileGeom g, const cpx<float>* __restrict__ tw,
                                const int64_t* __restrict__ pj, const float* __restrict__ cw, float* __restrict__ B) {
@@ -306,6 +625,21 @@ __global__ void build_b_kernel(ContractArgs a, TileGeom g, const cpx<float>* __r
 
 int round16(int x) { return (x + 15) / 16 * 16; }
 
+// The bulk copies of the pipelined kernel start on 16-byte boundaries and move
+// whole 16-byte units: the long operand's base, its row stride and its row
+// count must keep every copied row slice 16-byte aligned.
+bool pipe_ok(const ContractArgs& a, rsv_operator op) {
+  static const int env = [] {
+    const char* e = getenv("RSV_CONTRACT_PIPE");
+    return e != nullptr && e[0] == '0' ? 0 : 1;
+  }();
+  if (!env || op->sm_count <= 0) return false;
+  if ((reinterpret_cast<uintptr_t>(a.src) & 15u) != 0) return false;
+  if (a.mode == ANAL_R) return a.rows % 4 == 0;
+  if (a.mode == ANAL_C) return a.rows % 2 == 0;
+  return a.rows % 2 == 0 && a.src_stride % 2 == 0;
+}
+
 cudaError_t run(ContractArgs& a, const TileGeom& g, rsv_operator op) {
   const size_t bbytes = (size_t)(a.K / kKc) * 2 * kBStageFloats * sizeof(float);
   if (ensure(op->ws_tcb, bbytes) != RSV_OK) return cudaErrorMemoryAllocation;
@@ -317,10 +651,16 @@ cudaError_t run(ContractArgs& a, const TileGeom& g, rsv_operator op) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(tc_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    cudaFuncSetAttribute(tc_contract_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeSmem);
     attr_set = true;
   }
-  const unsigned blocks = (unsigned)((a.rows + kRowsCta - 1) / kRowsCta);
-  tc_contract_kernel<<<blocks, 256, kSmem, op->stream>>>(a);
+  const int64_t tiles = (a.rows + kRowsCta - 1) / kRowsCta;
+  if (pipe_ok(a, op)) {
+    const unsigned blocks = (unsigned)std::min<int64_t>(tiles, (int64_t)op->sm_count);
+    tc_contract_pipe_kernel<<<blocks, kPipeThreads, kPipeSmem, op->stream>>>(a);
+  } else {
+    tc_contract_kernel<<<(unsigned)tiles, 256, kSmem, op->stream>>>(a);
+  }
   return cudaGetLastError();
 }
 

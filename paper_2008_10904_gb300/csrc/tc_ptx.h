@@ -29,9 +29,23 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
-// Wait for the phase with the given parity to complete; false after `max_tries` polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_tries) {
+// Nanosecond global timer.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Upper bound of any single wait: 2 seconds of wall time.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Wait for the phase with the given parity to complete; false after `max_tries`
+// polls or kWaitLimitNs, whichever comes first, or (when `abort_flag` is given)
+// once *abort_flag is non-zero.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_tries,
+                                          const volatile int* abort_flag = nullptr) {
   const uint32_t a = smem_u32(bar);
+  uint64_t t0 = 0;
   for (uint32_t i = 0; i < max_tries; ++i) {
     uint32_t done;
     asm volatile(
@@ -42,6 +56,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((i & 63) == 63) {
+      if (abort_flag != nullptr && *abort_flag) return false;
+      const uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitLimitNs) return false;
+    }
   }
   return false;
 }
@@ -168,6 +188,25 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Release-ordered atomic add without a return value (fire and forget).
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Spin (one thread) until *p >= target, bounded by kWaitLimitNs; also stops once *err != 0.
+__device__ __forceinline__ bool spin_until_geq(const int* p, int target, const volatile int* err) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    if (ld_acquire(p) >= target) return true;
+    if ((i & 15) == 15) {
+      if (*err != 0) return false;
+      const uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitLimitNs) return false;
+    }
+  }
+}
+
 // Generic-proxy global writes become visible to the async proxy (bulk copies), and back.
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");

@@ -152,14 +152,14 @@ def test_dense_full_size_sampled(rsv):
 
 @pytest.mark.parametrize("n,x_half", [(128, 30.0), (256, 40.0)])
 @pytest.mark.parametrize("adjoint", [False, True])
-@pytest.mark.parametrize("path", ["persistent", "per_step", "cuda_cores"])
-def test_dense_tensor_core_step(rsv, n, x_half, adjoint, path, monkeypatch):
-    """FP32 dense march on the tcgen05 paths (persistent tile kernel, one launch per step) and on
-    the CUDA-core step, vs the oracle."""
+@pytest.mark.parametrize("path,k", [("persistent", 5), ("persistent", 20), ("per_step", 5), ("cuda_cores", 5)])
+def test_dense_tensor_core_step(rsv, n, x_half, adjoint, path, k, monkeypatch):
+    """FP32 dense march on the tcgen05 paths (persistent tile kernel with one or two vector
+    chains, one launch per step) and on the CUDA-core step, vs the oracle."""
     monkeypatch.setenv("RSV_DENSE_TENSOR", "0" if path == "cuda_cores" else "1")
     monkeypatch.setenv("RSV_DENSE_PERSISTENT", "0" if path == "per_step" else "1")
     sysm = W.Dense(n=n, x_half_width=x_half)
-    w = W.Workload("dense_tc", sysm, np.linspace(-1.0, 1.0, 8), 0.01, 5, "trm", tail_steps=2200)
+    w = W.Workload("dense_tc", sysm, np.linspace(-1.0, 1.0, 8), 0.01, k, "trm", tail_steps=2200)
     a = W.hermite_gl_matrix(sysm)
     op = rsv.create_for_workload(w, 1, dense_matrix=a)
     try:
