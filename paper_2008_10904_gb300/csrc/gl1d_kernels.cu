@@ -19,8 +19,8 @@
 namespace rsv {
 namespace {
 
-template <typename R, int PPT>
-__global__ void __launch_bounds__(1024) gl1d_tile_kernel(Gl1dTile t, cpx<R>* __restrict__ u,
+template <typename R, int PPT, int MAXT>
+__global__ void __launch_bounds__(MAXT) gl1d_tile_kernel(Gl1dTile t, cpx<R>* __restrict__ u,
                                                          const cpx<R>* __restrict__ F, cpx<R>* __restrict__ Y,
                                                          double* __restrict__ norms, int* __restrict__ flag) {
   extern __shared__ unsigned char smem_raw[];
@@ -81,51 +81,68 @@ __global__ void __launch_bounds__(1024) gl1d_tile_kernel(Gl1dTile t, cpx<R>* __r
     }
     buf ^= 1;
   };
-  cpx<R> f0[PPT], fh[PPT], f1[PPT];
+  // Forcing of step s: f(t_n + h/2) and f(t_n + h); f(t_n) is the previous
+  // step's f(t_n + h).  The loads for step s + 1 are issued at the start of
+  // step s, so their latency overlaps the step.
+  auto load_f = [&](int s, cpx<R>* fh_out, cpx<R>* f1_out) {
+    const bool forced = (F != nullptr) && (t.n0 + s < t.n_forced);
 #pragma unroll
-  for (int m = 0; m < PPT; ++m) f0[m] = fh[m] = f1[m] = zero;
+    for (int m = 0; m < PPT; ++m) {
+      fh_out[m] = f1_out[m] = zero;
+      if (forced && ok[m]) {
+        const int64_t r = rbase + threadIdx.x + m * blockDim.x;
+        fh_out[m] = F[(int64_t)(2 * s + 1) * rows + r];
+        f1_out[m] = F[(int64_t)(2 * s + 2) * rows + r];
+      }
+    }
+  };
+  cpx<R> f0[PPT], fh[PPT], f1[PPT], nfh[PPT], nf1[PPT];
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) f0[m] = nfh[m] = nf1[m] = zero;
   if (F != nullptr && t.n0 < t.n_forced) {
 #pragma unroll
     for (int m = 0; m < PPT; ++m)
       if (ok[m]) f0[m] = F[rbase + threadIdx.x + m * blockDim.x];
   }
+  load_f(0, fh, f1);
   for (int s = 0; s < t.steps; ++s) {
-    const int64_t n = t.n0 + s;
-    const bool forced = (F != nullptr) && (n < t.n_forced);
-    if (forced) {
+    if (s + 1 < t.steps) load_f(s + 1, nfh, nf1);
+    if (!((F != nullptr) && (t.n0 + s < t.n_forced))) {
 #pragma unroll
-      for (int m = 0; m < PPT; ++m) {
-        if (ok[m]) {
-          const int64_t r = rbase + threadIdx.x + m * blockDim.x;
-          fh[m] = F[(int64_t)(2 * s + 1) * rows + r];
-          f1[m] = F[(int64_t)(2 * s + 2) * rows + r];
-        }
-      }
-    } else {
-#pragma unroll
-      for (int m = 0; m < PPT; ++m) f0[m] = fh[m] = f1[m] = zero;
+      for (int m = 0; m < PPT; ++m) f0[m] = zero;   // unforced steps carry no forcing at any stage
     }
     if (Y != nullptr && s >= t.y_first) {
 #pragma unroll
       for (int m = 0; m < PPT; ++m)
         if (ok[m]) Y[(int64_t)s * rows + rbase + threadIdx.x + m * blockDim.x] = us[m];
     }
-    cpx<R> k1[PPT], k2[PPT], k3[PPT], k4[PPT], x[PPT];
-    stage(us, f0, k1);
-#pragma unroll
-    for (int m = 0; m < PPT; ++m) x[m] = us[m] + h2 * k1[m];
-    stage(x, fh, k2);
-#pragma unroll
-    for (int m = 0; m < PPT; ++m) x[m] = us[m] + h2 * k2[m];
-    stage(x, fh, k3);
-#pragma unroll
-    for (int m = 0; m < PPT; ++m) x[m] = us[m] + h * k3[m];
-    stage(x, f1, k4);
+    // k1 + 2 k2 + 2 k3 accumulates in acc; x is the next stage input
+    cpx<R> k[PPT], x[PPT], acc[PPT];
+    stage(us, f0, k);
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
-      const cpx<R> sum = k1[m] + R(2) * k2[m] + R(2) * k3[m] + k4[m];
-      us[m] = us[m] + h6 * sum;
+      acc[m] = k[m];
+      x[m] = us[m] + h2 * k[m];
+    }
+    stage(x, fh, k);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      acc[m] = acc[m] + R(2) * k[m];
+      x[m] = us[m] + h2 * k[m];
+    }
+    stage(x, fh, k);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      acc[m] = acc[m] + R(2) * k[m];
+      x[m] = us[m] + h * k[m];
+    }
+    stage(x, f1, k);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      us[m] = us[m] + h6 * (acc[m] + k[m]);
       f0[m] = f1[m];
+      fh[m] = nfh[m];
+      f1[m] = nf1[m];
     }
   }
   double nrm = 0.0;
@@ -168,28 +185,31 @@ __global__ void gl1d_apply_kernel(Gl1dTile t, const cpx<R>* __restrict__ x, cpx<
   y[(int64_t)v * t.n + p] = acc;
 }
 
-template <typename R, int PPT>
-cudaError_t launch_ppt(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms, int* flag,
+template <typename R, int PPT, int MAXT>
+cudaError_t launch_ppt(const Gl1dTile& t, int threads, void* u, const void* F, void* Y, double* norms, int* flag,
                        cudaStream_t st) {
-  int threads = (t.max_n + PPT - 1) / PPT;
-  threads = ((threads + 31) / 32) * 32;
   const size_t smem = sizeof(cpx<R>) * 2 * (size_t)(t.max_n + 2);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(gl1d_tile_kernel<R, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(gl1d_tile_kernel<R, PPT, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)t.n_inst, (unsigned)t.kg);
-  gl1d_tile_kernel<R, PPT><<<grid, threads, smem, st>>>(t, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y, norms, flag);
+  gl1d_tile_kernel<R, PPT, MAXT><<<grid, threads, smem, st>>>(t, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y, norms,
+                                                               flag);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+// One CTA per (instance, vector); PPT points per thread, interleaved (point
+// i = thread + m * blockDim) so that every load and store is coalesced.
 template <typename R>
 cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms, int* flag,
                              cudaStream_t st) {
-  if (t.max_n <= 1024) return launch_ppt<R, 1>(t, u, F, Y, norms, flag, st);
-  if (t.max_n <= 2048) return launch_ppt<R, 2>(t, u, F, Y, norms, flag, st);
-  if (t.max_n <= 4096) return launch_ppt<R, 4>(t, u, F, Y, norms, flag, st);
-  return cudaErrorInvalidValue;
+  if (t.max_n > 4096) return cudaErrorInvalidValue;
+  const int ppt = t.max_n <= 1024 ? 1 : (t.max_n <= 2048 ? 2 : 4);
+  const int threads = (((t.max_n + ppt - 1) / ppt + 31) / 32) * 32;
+  if (ppt == 1) return launch_ppt<R, 1, 1024>(t, threads, u, F, Y, norms, flag, st);
+  if (ppt == 2) return launch_ppt<R, 2, 1024>(t, threads, u, F, Y, norms, flag, st);
+  return launch_ppt<R, 4, 1024>(t, threads, u, F, Y, norms, flag, st);
 }
 
 template <typename R>

@@ -19,6 +19,8 @@
 // and the coupling -(u . grad)U (into component x only) becomes
 // -dU/dx_c * x_x into every component c.
 #include <cmath>
+#include <cstdlib>
+#include <utility>
 #include <vector>
 
 #include "rsv_ops.h"
@@ -398,6 +400,127 @@ StGeom geom_of(rsv_operator op, int kg, bool adjoint) {
   return g;
 }
 
+// ---------------------------------------------------------------------------
+// 2-D system: one whole RK4 step per launch, the four stages in shared memory.
+//
+// A CTA owns a TX x TY tile of one vector's field.  It reads u on the tile plus
+// a 4-cell frame (one cell per stage), evaluates stage 1 on the tile plus 3
+// frame cells, stage 2 on the tile plus 2, stage 3 on the tile plus 1 and
+// stage 4 on the tile, so each stage's stencil finds its inputs computed by the
+// previous stage in shared memory.  Cells outside the domain hold zero
+// (homogeneous Dirichlet).  Per step the field is read once (the frame from
+// neighbouring tiles mostly through L2), the new field written once, and the
+// forcing read at the three stage times (frames included); the snapshot of u
+// is written on analysed steps.  The arithmetic of each stage is that of the
+// per-stage kernels above.
+// ---------------------------------------------------------------------------
+constexpr int kFTX = 64, kFTY = 32, kFH = 4;
+constexpr int kFW = kFTX + 2 * kFH, kFHH = kFTY + 2 * kFH;
+constexpr int kFThreads = 256;
+
+template <typename R>
+constexpr size_t adr2d_fused_smem() {
+  return sizeof(R) * (3 * (size_t)kFW * kFHH + (size_t)kFTX * kFTY);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kFThreads) adr2d_step_kernel(StGeom g, const R* __restrict__ uin,
+                                                               R* __restrict__ uout, const R* __restrict__ f0,
+                                                               const R* __restrict__ fh, const R* __restrict__ f1,
+                                                               R* __restrict__ ysnap, R h) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* su = reinterpret_cast<R*>(smem_raw);     // u on the frame
+  R* sx = su + kFW * kFHH;                     // stage-2 input, later stage-4 input
+  R* sy = sx + kFW * kFHH;                     // stage-3 input
+  R* sacc = sy + kFW * kFHH;                   // u + h/6 k1 + h/3 k2 + h/3 k3 on the tile
+  const int nx = g.nx, ny = g.ny;
+  const int X0 = blockIdx.x * kFTX - kFH, Y0 = blockIdx.y * kFTY - kFH;
+  const int64_t base = (int64_t)blockIdx.z * g.n;
+  const R* U = reinterpret_cast<const R*>(g.f0);
+  const R* rr = reinterpret_cast<const R*>(g.f1);
+  const R idx2 = R(1) / (R(g.dx) * R(g.dx)), idy2 = R(1) / (R(g.dy) * R(g.dy));
+  const R i2dx = R(0.5) / R(g.dx), nu = R(g.visc);
+  const R cy = nu * idy2;
+  for (int e = threadIdx.x; e < kFW * kFHH; e += kFThreads) {
+    const int li = e % kFW, lj = e / kFW;
+    const int gi = X0 + li, gj = Y0 + lj;
+    su[e] = (gi >= 0 && gi < nx && gj >= 0 && gj < ny) ? uin[base + (int64_t)gj * nx + gi] : R(0);
+  }
+  __syncthreads();
+  // k = A x at frame cell (li, lj) of the shared field x, plus the forcing value
+  auto apply = [&](const R* x, int li, int lj, int gi, int gj, R fv) -> R {
+    const int e = lj * kFW + li;
+    const R ux = g.adjoint ? -U[gj] : U[gj];
+    const R cw = ux * i2dx + nu * idx2, ce = -ux * i2dx + nu * idx2;
+    const R cc = R(-2) * nu * (idx2 + idy2) + rr[gj] - sponge<R>(gi, gj, g);
+    return cw * x[e - 1] + ce * x[e + 1] + cy * (x[e - kFW] + x[e + kFW]) + cc * x[e] + fv;
+  };
+#pragma unroll 1
+  for (int stage = 1; stage <= 3; ++stage) {
+    const int m = stage;                              // frame cells skipped on each side
+    const int w = kFW - 2 * m, hh = kFHH - 2 * m;
+    const R* xin = stage == 1 ? su : stage == 2 ? sx : sy;
+    R* xout = stage == 1 ? sx : stage == 2 ? sy : sx;
+    const R* f = stage == 1 ? f0 : fh;
+    const R cx = stage == 3 ? h : R(0.5) * h;
+    const R ca = stage == 1 ? h / R(6) : h / R(3);
+    for (int e = threadIdx.x; e < w * hh; e += kFThreads) {
+      const int li = m + e % w, lj = m + e / w;
+      const int gi = X0 + li, gj = Y0 + lj;
+      const int le = lj * kFW + li;
+      R xo = R(0);
+      if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+        const int64_t p = base + (int64_t)gj * nx + gi;
+        const R k = apply(xin, li, lj, gi, gj, f != nullptr ? f[p] : R(0));
+        const R uu = su[le];
+        xo = uu + cx * k;
+        const int ti = li - kFH, tj = lj - kFH;
+        if (ti >= 0 && ti < kFTX && tj >= 0 && tj < kFTY) {
+          if (stage == 1) {
+            sacc[tj * kFTX + ti] = uu + ca * k;
+            if (ysnap != nullptr) ysnap[p] = uu;
+          } else {
+            sacc[tj * kFTX + ti] += ca * k;
+          }
+        }
+      }
+      // stage 3 writes into the stage-2 input: the barrier after stage 2 separates them
+      xout[le] = xo;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < kFTX * kFTY; e += kFThreads) {
+    const int ti = e % kFTX, tj = e / kFTX;
+    const int li = kFH + ti, lj = kFH + tj;
+    const int gi = X0 + li, gj = Y0 + lj;
+    if (gi < nx && gj < ny) {
+      const int64_t p = base + (int64_t)gj * nx + gi;
+      const R k = apply(sx, li, lj, gi, gj, f1 != nullptr ? f1[p] : R(0));
+      uout[p] = sacc[e] + (h / R(6)) * k;
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_adr2d_step(rsv_operator op, const StGeom& g, const R* uin, R* uout, const R* f0, const R* fh,
+                              const R* f1, R* ysnap, R h) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(adr2d_step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)adr2d_fused_smem<R>());
+    attr = true;
+  }
+  dim3 grid((unsigned)((g.nx + kFTX - 1) / kFTX), (unsigned)((g.ny + kFTY - 1) / kFTY), (unsigned)g.kg);
+  adr2d_step_kernel<R><<<grid, kFThreads, adr2d_fused_smem<R>(), op->stream>>>(g, uin, uout, f0, fh, f1, ysnap, h);
+  return cudaGetLastError();
+}
+
+// RSV_STENCIL_FUSED=0 selects the per-stage kernels (read at each march tile).
+bool adr2d_fused_enabled() {
+  const char* e = getenv("RSV_STENCIL_FUSED");
+  return !(e != nullptr && e[0] == '0');
+}
+
 template <typename R, int STAGE>
 cudaError_t launch_stage(rsv_operator op, const StGeom& g, const R* xin, const R* u, R* acc, const R* f, R* xout,
                          R* ysnap, R h) {
@@ -511,6 +634,25 @@ cudaError_t stencil_march_tile(rsv_operator op, const MarchTile& t, void* state,
   R* acc = xb + rows;
   const R h = (R)op->h;
   cudaError_t e = cudaSuccess;
+  if (op->kind == RSV_OP_ADR2D && adr2d_fused_enabled()) {
+    // whole steps, the field ping-pongs between u and xa
+    R* cur = u;
+    R* nxt = xa;
+    for (int s = 0; s < t.steps && e == cudaSuccess; ++s) {
+      const int64_t n = t.n0 + s;
+      const bool forced = F != nullptr && n < t.n_forced;
+      const R* Fr = static_cast<const R*>(F);
+      const R* f0 = forced ? Fr + (size_t)(2 * s) * rows : nullptr;
+      const R* fh = forced ? Fr + (size_t)(2 * s + 1) * rows : nullptr;
+      const R* f1 = forced ? Fr + (size_t)(2 * s + 2) * rows : nullptr;
+      R* ys = (Y != nullptr && s >= t.y_first) ? static_cast<R*>(Y) + (size_t)s * rows : nullptr;
+      e = launch_adr2d_step<R>(op, g, cur, nxt, f0, fh, f1, ys, h);
+      std::swap(cur, nxt);
+    }
+    if (e == cudaSuccess && cur != u) e = cudaMemcpyAsync(u, cur, sizeof(R) * rows, cudaMemcpyDeviceToDevice, op->stream);
+    if (e == cudaSuccess) e = check_finite(op, u, rows, true);
+    return e;
+  }
   for (int s = 0; s < t.steps && e == cudaSuccess; ++s) {
     const int64_t n = t.n0 + s;
     const bool forced = F != nullptr && n < t.n_forced;

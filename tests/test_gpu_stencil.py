@@ -46,6 +46,15 @@ def _adr_odd(variant="ssrm", omegas=None, k=3):
                       n_power_iter=1, real_state=True, seed=W.SEED_BASE + 34)
 
 
+def _adr_multi(variant="ssrm", omegas=None, k=2):
+    """Several fused-kernel tiles (64 x 32) in each direction, ragged at the far edges."""
+    sysm = W.ADR2D(nx=150, ny=70, lx=40.0, ly=10.0, sponge_cells=6)
+    om = np.linspace(0.0, 4.0, 8) if omegas is None else omegas
+    dx = sysm.lx / (sysm.nx + 1)
+    return W.Workload("adr_multi", sysm, om, 0.5 * dx, k, variant, n_transient_windows=1, tail_steps=60,
+                      n_power_iter=1, real_state=True, seed=W.SEED_BASE + 35)
+
+
 def _adv_small(variant="ssrm", k=2):
     sysm = W.ADV3D(nx=12, ny=8, nz=6, lx=20.0, ly=10.0, lz=10.0, visc=0.02)
     om = np.array([0.04 * np.pi * 5 * j for j in range(6)])
@@ -163,3 +172,27 @@ def test_stencil_full_grid_fp32_vs_fp64(rsv, make):
         finally:
             rsv.rsv_destroy_operator(op)
     assert _relerr(outs[1], outs[0]) < 1e-4
+
+
+@pytest.mark.parametrize("make", [_adr_small, _adr_multi])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("path", ["fused", "staged"])
+def test_adr2d_step_paths(rsv, make, prec, adjoint, path, monkeypatch):
+    """2-D march with the whole-step kernel (four stages in shared memory) and with the per-stage
+    kernels, vs the oracle."""
+    monkeypatch.setenv("RSV_STENCIL_FUSED", "1" if path == "fused" else "0")
+    w = make("trm")
+    op = rsv.create_for_workload(w, prec)
+    try:
+        fh = W.test_block(w)
+        if prec == 1:
+            fh = fh.astype(np.complex64).astype(np.complex128)
+        x = _dev(fh, prec)
+        y = x * 0
+        f = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
+        f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=15))
+        ref = _oracle(w, _matrix(w), fh, adjoint)
+        assert _relerr(y.cpu().numpy().astype(np.complex128), ref) < (TOL64 if prec == 0 else TOL32)
+    finally:
+        rsv.rsv_destroy_operator(op)
