@@ -107,9 +107,23 @@ typedef struct {
 typedef struct {
   int32_t variant;              /* rsv_variant                                      */
   int32_t n_transient_windows;  /* SSRM: forced windows before the analysed one     */
-  int64_t tail_steps;           /* TRM: unforced steps after the forcing window     */
+  int64_t tail_steps;           /* TRM: unforced steps after the forcing window
+                                   (the cap on the tail when tail_tol > 0)          */
   int32_t tile_steps;           /* steps per time tile S (0 = library default)      */
-  int32_t reserved;
+  int32_t reserved;             /* must be 0                                        */
+  double tail_tol;              /* TRM: 0 = march the whole tail; > 0 = truncate the
+                                   record by the state norm (Sec. 2.2; Sec. 3 marches
+                                   until the norm is below 1e-9, Sec. 4 until it is
+                                   1e-3 of its maximum).  At the end of every time
+                                   tile the library takes each vector's 2-norm over
+                                   the whole state; the march ends at the first tile
+                                   end at or after the end of the forcing window
+                                   where every vector of the group is at most
+                                   tail_tol times the largest norm it had at any tile
+                                   end so far.  Check points are therefore the tile
+                                   ends: multiples of the tile length reported by
+                                   rsv_describe ("tile="), and the last step.  SSRM
+                                   ignores it.  Negative or NaN: INVALID_ARG.       */
 } rsv_march_opts;
 
 /* Create an operator.  desc: system description (read during the call only).

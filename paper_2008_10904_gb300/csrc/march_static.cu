@@ -69,6 +69,8 @@ rsv_status march_static_impl(rsv_operator op, const void* in, int k, const rsv_m
     forced = total;
   } else if (o->variant == RSV_TRM) {
     if (o->tail_steps < 0) return fail(RSV_ERR_INVALID_ARG, "tail_steps < 0");
+    if (o->tail_tol != 0.0)
+      return fail(RSV_ERR_INVALID_ARG, "the allocation-free march runs the whole TRM tail: tail_tol must be 0");
     total = op->n_t + o->tail_steps;
     first = 0;
     forced = op->n_t;

@@ -1,6 +1,7 @@
 // Operator kinds: construction of the device coefficient arrays and the
 // dispatch of one march tile / one operator application to each kind's
 // kernels.
+#include <cstdlib>
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -105,6 +106,10 @@ int march_tile_kernels(rsv_operator op, int steps, int kg) {
     case RSV_OP_DENSE:
       if (op->prec == RSV_PREC_FP32 && dense_tc_supported(op, kg)) return op->tc_persistent ? 2 : steps + 1;
       return steps + 1;
+    case RSV_OP_ADR2D: {
+      const char* e = getenv("RSV_STENCIL_FUSED");
+      return (e != nullptr && e[0] == '0') ? 4 * steps + 1 : steps + 1;   // whole-step kernel by default
+    }
     default:
       return 4 * steps + 1;
   }
@@ -146,7 +151,45 @@ __global__ void finite_kernel(const T* __restrict__ x, int64_t count, int* flag)
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
 }
+
+// out[v] += sum of squares of vector v's values (FP64 sums; out zeroed by the caller).
+template <typename T>
+__global__ void vec_sumsq_kernel(const T* __restrict__ x, int64_t vals_per_vec, double* __restrict__ out) {
+  const T* xv = x + (int64_t)blockIdx.y * vals_per_vec;
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < vals_per_vec; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)xv[e];
+    acc += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    atomicAdd(out + blockIdx.y, t);
+  }
+}
 }  // namespace
+
+// Squared 2-norm of each of the kg vectors of the march state after step n_end
+// (the dense path keeps two step-parity copies of the state).
+cudaError_t state_sq_norms(rsv_operator op, int kg, int64_t n_end, double* d_out) {
+  const size_t elem = op->prec == RSV_PREC_FP64 ? 8 : 4;
+  const int64_t vals = (op->real_state ? 1 : 2) * op->n;
+  const char* st = static_cast<const char*>(op->ws_state.ptr);
+  if (op->kind == RSV_OP_DENSE) st += (size_t)(n_end & 1) * (size_t)kg * vals * elem;
+  cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * kg, op->stream);
+  if (e != cudaSuccess) return e;
+  const unsigned bx = (unsigned)std::min<int64_t>((vals + 255) / 256, std::max(1, 2 * op->sm_count / std::max(kg, 1)));
+  dim3 grid(std::max(bx, 1u), (unsigned)kg);
+  if (op->prec == RSV_PREC_FP64)
+    vec_sumsq_kernel<double><<<grid, 256, 0, op->stream>>>((const double*)st, vals, d_out);
+  else
+    vec_sumsq_kernel<float><<<grid, 256, 0, op->stream>>>((const float*)st, vals, d_out);
+  return cudaGetLastError();
+}
 
 cudaError_t check_finite(rsv_operator op, const void* state, int64_t count, bool real_state) {
   const int64_t vals = real_state ? count : 2 * count;

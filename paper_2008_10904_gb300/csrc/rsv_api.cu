@@ -221,6 +221,11 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
   if (!op || !buf || buflen < 1) return fail(RSV_ERR_INVALID_ARG, "bad describe arguments");
   static const char* kinds[] = {"gl1d", "dense", "adr2d", "adv3d"};
   const char* path = "cuda-core stages";
+  if (op->kind == RSV_OP_GL1D) path = "cuda-core tile kernel";
+  if (op->kind == RSV_OP_ADR2D) {
+    const char* e = getenv("RSV_STENCIL_FUSED");
+    if (!(e != nullptr && e[0] == '0')) path = "cuda-core whole-step kernel";
+  }
   if (op->kind == RSV_OP_DENSE) {
     if (op->prec == RSV_PREC_FP32 && op->tc_tiles[0] && !op->tc_disabled)
       path = op->tc_persistent ? "tcgen05 3xTF32 persistent tile kernel" : "tcgen05 3xTF32 one launch per step";
@@ -230,10 +235,10 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
   const char* contract = (op->prec == RSV_PREC_FP32 && !op->tc_contract_disabled) ? "tcgen05" : "cuda-core";
   snprintf(buf, (size_t)buflen,
            "kind=%s precision=%s n=%lld instances=%d path=%s contractions=%s resident_ctas=%d sms=%d tile=%d "
-           "group=%d",
+           "group=%d steps=%lld",
            (op->kind >= 0 && op->kind < 4) ? kinds[op->kind] : "?", op->prec == RSV_PREC_FP64 ? "fp64" : "fp32",
            (long long)op->n, op->n_inst, path, contract, op->tc_max_clusters, op->sm_count, op->last_tile,
-           op->last_group);
+           op->last_group, (long long)op->last_steps);
   return RSV_OK;
 }
 
@@ -372,6 +377,7 @@ static rsv_status make_schedule(rsv_operator op, const rsv_march_opts* o, Schedu
     s->forced = s->total;
   } else if (o->variant == RSV_TRM) {
     if (o->tail_steps < 0) return fail(RSV_ERR_INVALID_ARG, "tail_steps < 0");
+    if (!(o->tail_tol >= 0.0)) return fail(RSV_ERR_INVALID_ARG, "tail_tol must be >= 0");
     s->total = op->n_t + o->tail_steps;
     s->first = 0;
     s->forced = op->n_t;
@@ -465,6 +471,9 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
     }
     if (st != RSV_OK) return st;
     g.tau_stride = synth_stride;
+    // TRM truncation by the state norm: per-vector peak over the tile ends so far
+    const bool truncate = opts != nullptr && opts->variant == RSV_TRM && opts->tail_tol > 0.0;
+    std::vector<double> peak(truncate ? kv : 0, 0.0), nrm(truncate ? kv : 0, 0.0);
     for (int64_t n0 = 0; n0 < sc.total; n0 += S) {
       g.n0 = n0;
       g.steps = (int)std::min<int64_t>(S, sc.total - n0);
@@ -508,7 +517,24 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
         }
         if (e != cudaSuccess) return cuda_fail(e, "analysis");
       }
+      if (truncate) {
+        const int64_t n_end = n0 + g.steps;
+        e = state_sq_norms(op, kv, n_end, (double*)op->ws_norm.ptr);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(nrm.data(), op->ws_norm.ptr, sizeof(double) * kv, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, "tail norm");
+        bool small = true;
+        for (int v = 0; v < kv; ++v) {
+          const double r = std::sqrt(nrm[v]);
+          peak[v] = std::max(peak[v], r);
+          if (!(r <= opts->tail_tol * peak[v])) small = false;
+        }
+        op->last_steps = n_end;
+        if (n_end >= sc.forced && small) break;
+      }
     }
+    if (!truncate) op->last_steps = sc.total;
     void* o = static_cast<char*>(out) + (size_t)v0 * n * ce;
     e = launch_finish<R>(acc, acc_stride, op->n_omega, rows, 1.0 / (double)op->n_t, o, (int64_t)k * n, stream);
     if (e != cudaSuccess) return cuda_fail(e, "finish");

@@ -146,6 +146,7 @@ struct rsv_operator_s {
   int* d_flag = nullptr;
   rsv::Profiler prof;
   int last_tile = 0, last_group = 0;   // tile length and vector-group size of the latest march
+  int64_t last_steps = 0;              // steps marched by the latest march's last vector group
 
   ~rsv_operator_s();
 };

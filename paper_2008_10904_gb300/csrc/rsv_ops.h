@@ -42,6 +42,7 @@ rsv_status on_frequencies(rsv_operator op);
 
 // Sets the flag if the state block holds a NaN / Inf (kinds without an in-kernel norm monitor).
 cudaError_t check_finite(rsv_operator op, const void* state, int64_t count, bool real_state);
+cudaError_t state_sq_norms(rsv_operator op, int kg, int64_t n_end, double* d_out);
 
 // dense kind (dense_kernels.cu)
 rsv_status dense_on_frequencies(rsv_operator op);

@@ -420,7 +420,17 @@ constexpr int kFThreads = 256;
 
 template <typename R>
 constexpr size_t adr2d_fused_smem() {
-  return sizeof(R) * (3 * (size_t)kFW * kFHH + (size_t)kFTX * kFTY);
+  // u, two stage inputs and the forcing at t_n on the frame, forcing at t_n + h/2 and
+  // t_n + h, the accumulator, per-row coefficients
+  return sizeof(R) * (5 * (size_t)kFW * kFHH + 2 * (size_t)kFTX * kFTY + 3 * (size_t)kFHH);
+}
+
+// Asynchronous global -> shared copy of one element (no register staging).
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src),
+               "n"(sizeof(R))
+               : "memory");
 }
 
 template <typename R>
@@ -429,31 +439,59 @@ __global__ void __launch_bounds__(kFThreads) adr2d_step_kernel(StGeom g, const R
                                                                const R* __restrict__ fh, const R* __restrict__ f1,
                                                                R* __restrict__ ysnap, R h) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* su = reinterpret_cast<R*>(smem_raw);     // u on the frame
-  R* sx = su + kFW * kFHH;                     // stage-2 input, later stage-4 input
-  R* sy = sx + kFW * kFHH;                     // stage-3 input
-  R* sacc = sy + kFW * kFHH;                   // u + h/6 k1 + h/3 k2 + h/3 k3 on the tile
+  constexpr int kF = kFW * kFHH;
+  R* su = reinterpret_cast<R*>(smem_raw);      // u on the frame
+  R* sx = su + kF;                              // stage-2 input, later stage-4 input
+  R* sy = sx + kF;                              // stage-3 input
+  R* sf0 = sy + kF;                             // f(t_n) on the frame
+  R* sfh = sf0 + kF;                            // f(t_n + h/2) on the frame
+  R* sf1 = sfh + kF;                            // f(t_n + h) on the tile
+  R* sacc = sf1 + kFTX * kFTY;                  // u + h/6 k1 + h/3 k2 + h/3 k3 on the tile
+  R* rw = sacc + kFTX * kFTY;                   // per frame row: west, east, centre coefficients
+  R* re = rw + kFHH;
+  R* rc = re + kFHH;
   const int nx = g.nx, ny = g.ny;
   const int X0 = blockIdx.x * kFTX - kFH, Y0 = blockIdx.y * kFTY - kFH;
   const int64_t base = (int64_t)blockIdx.z * g.n;
-  const R* U = reinterpret_cast<const R*>(g.f0);
-  const R* rr = reinterpret_cast<const R*>(g.f1);
   const R idx2 = R(1) / (R(g.dx) * R(g.dx)), idy2 = R(1) / (R(g.dy) * R(g.dy));
   const R i2dx = R(0.5) / R(g.dx), nu = R(g.visc);
   const R cy = nu * idy2;
-  for (int e = threadIdx.x; e < kFW * kFHH; e += kFThreads) {
+  // every input of the step is copied into shared memory up front, all copies in flight at once
+  for (int e = threadIdx.x; e < kF; e += kFThreads) {
     const int li = e % kFW, lj = e / kFW;
     const int gi = X0 + li, gj = Y0 + lj;
-    su[e] = (gi >= 0 && gi < nx && gj >= 0 && gj < ny) ? uin[base + (int64_t)gj * nx + gi] : R(0);
+    const bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+    const int64_t p = base + (int64_t)gj * nx + gi;
+    if (in) cp_async_elem(su + e, uin + p);
+    else su[e] = R(0);
+    const bool r1 = li >= 1 && li < kFW - 1 && lj >= 1 && lj < kFHH - 1;   // stage-1 cells
+    const bool r2 = li >= 2 && li < kFW - 2 && lj >= 2 && lj < kFHH - 2;   // stage-2 and -3 cells
+    if (in && r1 && f0 != nullptr) cp_async_elem(sf0 + e, f0 + p);
+    else sf0[e] = R(0);
+    if (in && r2 && fh != nullptr) cp_async_elem(sfh + e, fh + p);
+    else sfh[e] = R(0);
   }
+  for (int e = threadIdx.x; e < kFTX * kFTY; e += kFThreads) {
+    const int gi = X0 + kFH + e % kFTX, gj = Y0 + kFH + e / kFTX;
+    if (gi < nx && gj < ny && f1 != nullptr) cp_async_elem(sf1 + e, f1 + base + (int64_t)gj * nx + gi);
+    else sf1[e] = R(0);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  if (threadIdx.x < kFHH) {
+    const int gj = min(max(Y0 + (int)threadIdx.x, 0), ny - 1);
+    const R U = reinterpret_cast<const R*>(g.f0)[gj];
+    const R ux = g.adjoint ? -U : U;
+    rw[threadIdx.x] = ux * i2dx + nu * idx2;
+    re[threadIdx.x] = -ux * i2dx + nu * idx2;
+    rc[threadIdx.x] = R(-2) * nu * (idx2 + idy2) + reinterpret_cast<const R*>(g.f1)[gj];
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   // k = A x at frame cell (li, lj) of the shared field x, plus the forcing value
   auto apply = [&](const R* x, int li, int lj, int gi, int gj, R fv) -> R {
     const int e = lj * kFW + li;
-    const R ux = g.adjoint ? -U[gj] : U[gj];
-    const R cw = ux * i2dx + nu * idx2, ce = -ux * i2dx + nu * idx2;
-    const R cc = R(-2) * nu * (idx2 + idy2) + rr[gj] - sponge<R>(gi, gj, g);
-    return cw * x[e - 1] + ce * x[e + 1] + cy * (x[e - kFW] + x[e + kFW]) + cc * x[e] + fv;
+    const R cc = rc[lj] - sponge<R>(gi, gj, g);
+    return rw[lj] * x[e - 1] + re[lj] * x[e + 1] + cy * (x[e - kFW] + x[e + kFW]) + cc * x[e] + fv;
   };
 #pragma unroll 1
   for (int stage = 1; stage <= 3; ++stage) {
@@ -461,7 +499,7 @@ __global__ void __launch_bounds__(kFThreads) adr2d_step_kernel(StGeom g, const R
     const int w = kFW - 2 * m, hh = kFHH - 2 * m;
     const R* xin = stage == 1 ? su : stage == 2 ? sx : sy;
     R* xout = stage == 1 ? sx : stage == 2 ? sy : sx;
-    const R* f = stage == 1 ? f0 : fh;
+    const R* sf = stage == 1 ? sf0 : sfh;
     const R cx = stage == 3 ? h : R(0.5) * h;
     const R ca = stage == 1 ? h / R(6) : h / R(3);
     for (int e = threadIdx.x; e < w * hh; e += kFThreads) {
@@ -470,15 +508,14 @@ __global__ void __launch_bounds__(kFThreads) adr2d_step_kernel(StGeom g, const R
       const int le = lj * kFW + li;
       R xo = R(0);
       if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
-        const int64_t p = base + (int64_t)gj * nx + gi;
-        const R k = apply(xin, li, lj, gi, gj, f != nullptr ? f[p] : R(0));
+        const R k = apply(xin, li, lj, gi, gj, sf[le]);
         const R uu = su[le];
         xo = uu + cx * k;
         const int ti = li - kFH, tj = lj - kFH;
         if (ti >= 0 && ti < kFTX && tj >= 0 && tj < kFTY) {
           if (stage == 1) {
             sacc[tj * kFTX + ti] = uu + ca * k;
-            if (ysnap != nullptr) ysnap[p] = uu;
+            if (ysnap != nullptr) ysnap[base + (int64_t)gj * nx + gi] = uu;
           } else {
             sacc[tj * kFTX + ti] += ca * k;
           }
@@ -494,9 +531,8 @@ __global__ void __launch_bounds__(kFThreads) adr2d_step_kernel(StGeom g, const R
     const int li = kFH + ti, lj = kFH + tj;
     const int gi = X0 + li, gj = Y0 + lj;
     if (gi < nx && gj < ny) {
-      const int64_t p = base + (int64_t)gj * nx + gi;
-      const R k = apply(sx, li, lj, gi, gj, f1 != nullptr ? f1[p] : R(0));
-      uout[p] = sacc[e] + (h / R(6)) * k;
+      const R k = apply(sx, li, lj, gi, gj, sf1[e]);
+      uout[base + (int64_t)gj * nx + gi] = sacc[e] + (h / R(6)) * k;
     }
   }
 }

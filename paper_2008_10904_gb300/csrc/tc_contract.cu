@@ -256,28 +256,32 @@ __global__ void __launch_bounds__(256, 1) tc_contract_kernel(ContractArgs a) {
 // Pipelined persistent variant (long operand streamed by bulk copies).
 //
 // One CTA per SM walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// with four warp roles connected by mbarrier rings:
-//   warp 8 (one thread)  producer: bulk-copies each K chunk of the long operand
+// with warp roles connected by mbarrier rings:
+//   warp 12 (one thread) producer: bulk-copies each K chunk of the long operand
 //                        in its storage precision into a 4-deep raw ring;
-//   warp 10 (one thread) producer: bulk-copies the chunk's pre-split twiddles
+//   warp 14 (one thread) producer: bulk-copies the chunk's pre-split twiddles
 //                        into a 2-deep B ring;
 //   warps 0-3            converters: one row each, raw value -> TF32 hi / lo in
 //                        the K-major operand layout (2 stages);
-//   warp 9 (one thread)  MMA issuer: 3 TF32 MMAs per K-step and N half into the
+//   warp 13 (one thread) MMA issuer: 3 TF32 MMAs per K-step and N half into the
 //                        tile's tensor-memory accumulator, commits release the
 //                        operand stages and, after the last chunk, the tile;
-//   warps 4-7            epilogue: tensor memory -> F, or += FP64 accumulators;
-//                        then release the accumulator for the next tile.
+//   warps 4-11           epilogue: two warps per tensor-memory lane quadrant,
+//                        each taking half of the columns, 32 columns per load;
+//                        tensor memory -> F, or += FP64 accumulators; then
+//                        release the accumulator for the next tile.
 // The chunk sequence runs on across tiles, so the next tile's operands stream
 // in during the current tile's epilogue.  Every wait is bounded and also
 // returns once another role has aborted; on abort the producer and the MMA
 // issuer drain what they issued (bounded) before the CTA frees tensor memory.
 // ---------------------------------------------------------------------------
+__host__ __device__ constexpr int round16c(int x) { return (x + 15) / 16 * 16; }
+
 constexpr int kRawRing = 4;
 constexpr int kAStages = 2;
 constexpr int kBRing = 2;
 constexpr uint32_t kRawBytes = kRowsCta * kKc * 4;   // 128 rows x 16 real K values
-constexpr int kPipeThreads = 352;
+constexpr int kPipeThreads = 480;                    // 15 warps, roles below
 constexpr uint32_t kPipeSmem =
     kRawRing * kRawBytes + kAStages * 2 * kAStageFloats * 4 + kBRing * 2 * kBStageFloats * 4 + 256;
 
@@ -365,43 +369,51 @@ __device__ __forceinline__ void convert_row(const ContractArgs& a, int64_t r0, i
   }
 }
 
-__device__ __forceinline__ void epilogue_tile(const ContractArgs& a, int64_t r, uint32_t tq, bool ok) {
-  for (int c = 0; c < a.N; c += 16) {
-    float v[16];
-    tc::tmem_ld16(tq + (uint32_t)c, v);
-    if (!ok || r >= a.rows) continue;
-    if (a.mode == SYNTH_C) {
-      cpx<float>* F = reinterpret_cast<cpx<float>*>(a.out);
+// Columns [c0, c1) of row r: F stores, or FP64 accumulator read-modify-writes,
+// 32 columns per tensor-memory load, all loads of a group issued before use.
+template <int W>
+__device__ __forceinline__ void epilogue_cols(const ContractArgs& a, int64_t r, uint32_t tq, int c, bool row_ok) {
+  float v[32];
+  if (W == 32) tc::tmem_ld32(tq + (uint32_t)c, v);
+  else tc::tmem_ld16(tq + (uint32_t)c, v);
+  if (!row_ok) return;
+  if (a.mode == SYNTH_C) {
+    float2* F = reinterpret_cast<float2*>(a.out);
 #pragma unroll
-      for (int q = 0; q < 16; q += 2) {
-        const int tau = (c + q) >> 1;
-        if (tau < a.n_tau) __stcs(reinterpret_cast<float2*>(F + (int64_t)(a.tau0 + tau) * a.rows + r), make_float2(v[q], v[q + 1]));
-      }
-    } else if (a.mode == SYNTH_R) {
-      float* F = reinterpret_cast<float*>(a.out);
+    for (int q = 0; q < W; q += 2) {
+      const int tau = (c + q) >> 1;
+      if (tau < a.n_tau) __stcs(F + (int64_t)(a.tau0 + tau) * a.rows + r, make_float2(v[q], v[q + 1]));
+    }
+  } else if (a.mode == SYNTH_R) {
+    float* F = reinterpret_cast<float*>(a.out);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int tau = c + q;
-        if (tau < a.n_tau) __stcs(F + (int64_t)(a.tau0 + tau) * a.rows + r, v[q]);
-      }
-    } else {
-      cpx<double>* __restrict__ acc = reinterpret_cast<cpx<double>*>(a.out);
-      double2 old[8];
+    for (int q = 0; q < W; ++q) {
+      const int tau = c + q;
+      if (tau < a.n_tau) __stcs(F + (int64_t)(a.tau0 + tau) * a.rows + r, v[q]);
+    }
+  } else {
+    double2* __restrict__ acc = reinterpret_cast<double2*>(a.out);
+    double2 old[W / 2];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int j = (c >> 1) + q;
-        old[q] = j < a.n_omega ? __ldcs(reinterpret_cast<const double2*>(acc + (int64_t)j * a.acc_stride + r))
-                               : make_double2(0.0, 0.0);
-      }
+    for (int q = 0; q < W / 2; ++q) {
+      const int j = (c >> 1) + q;
+      old[q] = j < a.n_omega ? __ldcs(acc + (int64_t)j * a.acc_stride + r) : make_double2(0.0, 0.0);
+    }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int j = (c >> 1) + q;
-        if (j < a.n_omega)
-          __stcs(reinterpret_cast<double2*>(acc + (int64_t)j * a.acc_stride + r),
-                 make_double2(old[q].x + (double)v[2 * q], old[q].y + (double)v[2 * q + 1]));
-      }
+    for (int q = 0; q < W / 2; ++q) {
+      const int j = (c >> 1) + q;
+      if (j < a.n_omega)
+        __stcs(acc + (int64_t)j * a.acc_stride + r,
+               make_double2(old[q].x + (double)v[2 * q], old[q].y + (double)v[2 * q + 1]));
     }
   }
+}
+
+__device__ __forceinline__ void epilogue_tile(const ContractArgs& a, int64_t r, uint32_t tq, int c0, int c1) {
+  const bool row_ok = r < a.rows;
+  int c = c0;
+  for (; c + 32 <= c1; c += 32) epilogue_cols<32>(a, r, tq, c, row_ok);
+  if (c < c1) epilogue_cols<16>(a, r, tq, c, row_ok);
 }
 
 __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(ContractArgs a) {
@@ -428,7 +440,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
       tc::mbar_init(&pb->b_empty[i], 1);
     }
     tc::mbar_init(&pb->acc_full, 1);
-    tc::mbar_init(&pb->acc_empty, 128);
+    tc::mbar_init(&pb->acc_empty, 256);
     pb->abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -441,7 +453,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
   const int64_t tiles = (a.rows + kRowsCta - 1) / kRowsCta;
   const uint32_t bchunk_bytes = 4u * (uint32_t)a.N * kKc;
 
-  if (warp == 8) {
+  if (warp == 12) {
     if (lane == 0) {  // producer of the long operand
       uint32_t g = 0;
       bool ok = true;
@@ -462,7 +474,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
         }
       }
     }
-  } else if (warp == 10) {
+  } else if (warp == 14) {
     if (lane == 0) {  // producer of the twiddle operand (the same chunks for every tile)
       uint32_t g = 0;
       bool ok = true;
@@ -485,7 +497,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
         }
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == 13) {
     if (lane == 0) {  // MMA issuer
       uint32_t g = 0, tt = 0;
       bool ok = true;
@@ -552,14 +564,16 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
       }
     }
     if (!ok) pabort(pb, a.err);
-  } else if (warp >= 4 && warp < 8) {  // epilogue, TMEM lane quadrant warp % 4
+  } else if (warp >= 4 && warp < 12) {  // epilogue: TMEM lane quadrant warp % 4, one half of the columns
     const int q = warp & 3;
+    const int half = round16c((a.N + 1) / 2);
+    const int c0 = warp < 8 ? 0 : half, c1 = warp < 8 ? half : a.N;
     uint32_t tt = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tt) {
       if (!pwait(&pb->acc_full, tt & 1, abort_flag)) { ok = false; break; }
       tc::tc_fence_after();
-      epilogue_tile(a, t * kRowsCta + 32 * q + lane, tmem + ((uint32_t)(32 * q) << 16), true);
+      epilogue_tile(a, t * kRowsCta + 32 * q + lane, tmem + ((uint32_t)(32 * q) << 16), c0, c1);
       tc::tc_fence_before();
       mbar_arrive(&pb->acc_empty);
     }

@@ -48,7 +48,8 @@ class rsv_operator_desc(ctypes.Structure):
 
 class rsv_march_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("n_transient_windows", ctypes.c_int32),
-                ("tail_steps", ctypes.c_int64), ("tile_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tail_steps", ctypes.c_int64), ("tile_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tail_tol", ctypes.c_double)]
 
 
 _lib = None
@@ -121,9 +122,9 @@ def _ptr(x) -> int:
     raise TypeError(type(x))
 
 
-def _opts(variant="ssrm", n_transient_windows=0, tail_steps=0, tile_steps=0):
+def _opts(variant="ssrm", n_transient_windows=0, tail_steps=0, tile_steps=0, tail_tol=0.0):
     return rsv_march_opts(RSV_SSRM if variant == "ssrm" else RSV_TRM, int(n_transient_windows),
-                          int(tail_steps), int(tile_steps), 0)
+                          int(tail_steps), int(tile_steps), 0, float(tail_tol))
 
 
 class Operator:

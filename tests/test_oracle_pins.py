@@ -81,6 +81,29 @@ def test_trm_tail_leakage_decays():
         assert 0.2 * expected < r < 5.0 * expected, (errs, expected)
 
 
+def test_trm_norm_truncation():
+    """Sec. 2.2 / Sec. 3: ending the TRM record once the state norm has fallen to tol times its
+    peak leaves a leakage error of the order of tol against the closed-form R_h fhat, and a
+    tighter tol marches longer."""
+    w, a, g = _small()
+    fh = W.test_block(w)
+    ref = _apply_r([resolvent.rk4_discrete(a, om, g.h) for om in g.omegas], fh)
+    prev = 0
+    for tol in (1e-3, 1e-6, 1e-9):
+        y, steps = march.march(a, g, fh, variant="trm", tail_steps=20 * g.n_t, tail_tol=tol, check_every=50,
+                               return_steps=True)
+        err = np.abs(y - ref).max() / np.abs(ref).max()
+        assert 1e-3 * tol < err < tol, (tol, err)
+        assert steps % 50 == 0 and steps >= g.n_t and steps > prev
+        prev = steps
+        # the first check point that meets the rule: at the one before, some vector was above it
+        _, u_before = march.march(a, g, fh, variant="trm", tail_steps=20 * g.n_t, stop_after=steps - 50,
+                                  return_state=True)
+        _, u_stop = march.march(a, g, fh, variant="trm", tail_steps=20 * g.n_t, stop_after=steps,
+                                return_state=True)
+        assert np.linalg.norm(u_before, axis=1).max() > np.linalg.norm(u_stop, axis=1).max()
+
+
 def test_frequency_orthogonality():
     """P8: forcing one grid frequency gives no response at the others (Sec. 2.3)."""
     w, a, g = _small()
