@@ -172,7 +172,9 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
                  1-D kind (state held on chip for the whole tile): the forcing tile read
                  (2S+1 stage times), the snapshot tile written (S steps) and the state read
                  and written once, (3S + 3) state passes per tile;
-                 stencil kinds: 15 state passes per step (12 for four stage read/write
+                 2-D whole-step kernel: 6 state passes per step (state read and written,
+                 forcing read at the three stage times, snapshot written);
+                 per-stage kernels: 15 state passes per step (12 for four stage read/write
                  pairs, 2 forcing reads, 1 snapshot write)
     """
     peaks = load_peaks()
@@ -207,6 +209,10 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
         work = 8.0 * w.n * w.n * w.k * S
         bound, unit, peak, per = "alu", "TFLOP/s", alu_peak, 1e12
         src = "derived FP32 CUDA-core rate"
+    elif cat == "march" and "whole-step" in path:
+        work = 6.0 * rows * se * S
+        bound, unit, peak, per = "hbm", "GB/s", peaks["hbm_gbs"], 1e9
+        src = peaks["src"] + " copy bandwidth"
     elif cat == "march" and "kind=gl1d" in path:
         work = (3.0 * S + 3.0) * rows * se
         bound, unit, peak, per = "hbm", "GB/s", peaks["hbm_gbs"], 1e9
@@ -254,7 +260,8 @@ def cpu_baseline(name: str, target_seconds: float = 15.0):
                 "sample": f"not run: the FP64 oracle would hold {w.n * w.k * w.n_omega * 16 / 2**30:.0f} GiB "
                           "of complex128 test block and accumulators on the host"}
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    probe = 10 if type(w.system).__name__ in ("Dense", "ADV3D") else 100
+    big = w.n * w.k * w.n_omega > (1 << 28)
+    probe = 3 if big else (10 if type(w.system).__name__ in ("Dense", "ADV3D") else 100)
     r = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, name=name, steps=probe)],
                        capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:

@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(256, 1) dense_tc_step_kernel(TcStepArgs a) {
 //   3. sum the three product groups out of tensor memory into the CTA's
 //      128 x 32 partial, store it (L2) and count it in the row block's counter;
 //   4. as owner of 64/CS rows of its row block, wait for all CS partials of the
-//      step, sum them, apply the RK4 update u <- u + D u + F (the owner keeps
+//      step, bulk-copy its rows of them into shared memory (16 KB), sum them,
+//      apply the RK4 update u <- u + D u + F (the owner keeps
 //      its rows of u in registers for the whole tile), write the snapshot and
 //      the hi / lo split of the new state, and count the publication.
 // Partials, split states and counter targets are double-buffered by step
@@ -205,7 +206,8 @@ constexpr int kChainN = 2 * kChainVec;               // real columns per chain (
 constexpr int kMaxChains = 2;
 constexpr uint32_t kXcFloats = 2 * kChainN * kTileK; // hi rows [0, 32) then lo rows [32, 64): 8192 floats
 constexpr uint32_t kPartFloats = kM * kChainN;       // 128 x 32 partial of one CTA
-constexpr uint32_t kSmemPersistent = 4 * (2 * kATileFloats + kMaxChains * kXcFloats) + 256;
+constexpr uint32_t kGFloats = 2 * kTileRows * kChainN;   // the owner's rows of all CS partials: 16 KB
+constexpr uint32_t kSmemPersistent = 4 * (2 * kATileFloats + kMaxChains * (kXcFloats + kGFloats)) + 256;
 constexpr int kMarchThreads = 128 * kMaxChains;
 
 struct TcMarchArgs {
@@ -234,8 +236,9 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
   float* A_hi = reinterpret_cast<float*>(smem);
   float* A_lo = A_hi + kATileFloats;
   float* Xs = A_lo + kATileFloats;                                          // [chain][kXcFloats]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Xs + kMaxChains * kXcFloats);  // [0] A, then 2 per chain
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 1 + 2 * kMaxChains);
+  float* Gs = Xs + kMaxChains * kXcFloats;                                  // [chain][kGFloats]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Gs + kMaxChains * kGFloats);  // [0] A, then 3 per chain
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + 1 + 3 * kMaxChains);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int chain = warp >> 2;                  // warps 4c .. 4c + 3 drive chain c
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
   const int j = blockIdx.x % a.cs;
   const volatile int* errv = a.err;
   if (tid == 0) {
-    for (int b = 0; b < 1 + 2 * kMaxChains; ++b) tc::mbar_init(&bars[b], 1);
+    for (int b = 0; b < 1 + 3 * kMaxChains; ++b) tc::mbar_init(&bars[b], 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tbase, 256);
@@ -263,8 +266,10 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
   __syncthreads();
   if (chain < a.chains) {
     float* X_sm = Xs + (size_t)chain * kXcFloats;
-    uint64_t* bar_x = &bars[1 + 2 * chain];
-    uint64_t* bar_m = &bars[2 + 2 * chain];
+    uint64_t* bar_x = &bars[1 + 3 * chain];
+    uint64_t* bar_m = &bars[2 + 3 * chain];
+    uint64_t* bar_g = &bars[3 + 3 * chain];
+    float* G_sm = Gs + (size_t)chain * kGFloats;   // [CS][re rows, im rows][rpc][kChainN]
     const uint32_t tcol = tmem + (uint32_t)(chain * 128);
     const size_t xset = (size_t)a.cs * kXcFloats;                // one parity
     float* Xg = a.X + (size_t)chain * 2 * xset;
@@ -383,30 +388,45 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
       tc::tc_fence_before();
       chain_bar(chain);
       if (ctid == 0) tc::red_release_add(&cnt[par * MB + mb], 1);
-      // 4. owner: all partials of the row block for this step
+      // 4. owner: all partials of the row block for this step; the owner's rows of every
+      //    partial (rpc real-part rows and rpc imaginary-part rows) come in by bulk copies
+      const float* pbase = partg + ((size_t)par * MB + mb) * a.cs * kPartFloats;
       if (ctid == 0) {
-        if (!tc::spin_until_geq(&cnt[par * MB + mb], a.cs * (int)((n >> 1) + 1), errv)) atomicExch(a.err, 2);
+        if (!tc::spin_until_geq(&cnt[par * MB + mb], a.cs * (int)((n >> 1) + 1), errv)) {
+          atomicExch(a.err, 2);
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar_g)) : "memory");
+        } else {
+          tc::fence_proxy_async_global();
+          const uint32_t rows_bytes = (uint32_t)rpc * kChainN * 4;
+          tc::mbar_arrive_expect_tx(bar_g, 2u * (uint32_t)a.cs * rows_bytes);
+          for (int p = 0; p < a.cs; ++p) {
+            const float* src = pbase + (size_t)p * kPartFloats;
+            float* dst = G_sm + (size_t)p * 2 * rpc * kChainN;
+            tc::bulk_g2s(dst, src + (size_t)(rpc * j) * kChainN, rows_bytes, bar_g);
+            tc::bulk_g2s(dst + rpc * kChainN, src + (size_t)(64 + rpc * j) * kChainN, rows_bytes, bar_g);
+          }
+        }
       }
-      chain_bar(chain);
-      ok = ok && *errv == 0;
+      if (!tc::mbar_wait(bar_g, (uint32_t)(s & 1), 0xFFFFFFFFu, errv)) atomicExch(a.err, 2);
       cpx<float>* Ys = (a.Y != nullptr && s >= a.y_first) ? a.Y + (size_t)s * rows : nullptr;
       float* xo_par = Xg + (size_t)(1 - par) * xset;
-      const float* pbase = partg + ((size_t)par * MB + mb) * a.cs * kPartFloats;
 #pragma unroll
       for (int q = 0; q < kMaxPairs; ++q) {
         const int pidx = ctid + 128 * q;
         if (pidx < npairs) {
-          const int iloc = rpc * j + (pidx >> 4);
+          const int il = pidx >> 4;
+          const int iloc = rpc * j + il;
           float prr = 0.f, pri = 0.f, pir = 0.f, pii = 0.f;
           float t0[8], t1[8], t2[8], t3[8];
 #pragma unroll
           for (int p = 0; p < 8; ++p) {
             if (p < a.cs) {
-              const float* pp = pbase + (size_t)p * kPartFloats;
-              t0[p] = __ldcg(pp + iloc * kChainN + vl);
-              t1[p] = __ldcg(pp + iloc * kChainN + kChainVec + vl);
-              t2[p] = __ldcg(pp + (64 + iloc) * kChainN + vl);
-              t3[p] = __ldcg(pp + (64 + iloc) * kChainN + kChainVec + vl);
+              const float* gr = G_sm + (size_t)p * 2 * rpc * kChainN + il * kChainN;
+              const float* gi = gr + rpc * kChainN;
+              t0[p] = gr[vl];
+              t1[p] = gr[kChainVec + vl];
+              t2[p] = gi[vl];
+              t3[p] = gi[kChainVec + vl];
             }
           }
 #pragma unroll

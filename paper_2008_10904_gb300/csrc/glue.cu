@@ -129,17 +129,20 @@ cudaError_t gram_to_host(rsv_operator op, const void* X, int k, std::vector<cd>&
 template <typename R>
 cudaError_t combine_from_host(rsv_operator op, const void* in, int ka, int kb, const std::vector<cd>& M, void* out,
                               int out_k) {
-  const size_t bytes = M.size() * sizeof(cpx<double>);
+  // the small matrices go to the device in the block's precision (the kernel computes in it)
+  std::vector<cpx<R>> Mr(M.size());
+  for (size_t i = 0; i < M.size(); ++i) Mr[i] = mk<R>((R)M[i].real(), (R)M[i].imag());
+  const size_t bytes = Mr.size() * sizeof(cpx<R>);
   if (ensure(op->ws_small, bytes) != RSV_OK) return cudaErrorMemoryAllocation;
-  cudaError_t e = cudaMemcpyAsync(op->ws_small.ptr, M.data(), bytes, cudaMemcpyHostToDevice, op->stream);
-  if (e != cudaSuccess) return e;
-  {
+  cudaError_t e = cudaMemcpyAsync(op->ws_small.ptr, Mr.data(), bytes, cudaMemcpyHostToDevice, op->stream);
+  if (e == cudaSuccess) {
     ProfScope ps(op, PROF_GLUE);
     e = launch_combine<R>(in, op->n_omega, ka, kb, op->n, (const int32_t*)op->d_inst_of_point, op->n_inst,
-                          (const cpx<double>*)op->ws_small.ptr, out, out_k, op->stream);
+                          op->ws_small.ptr, out, out_k, op->stream);
   }
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(op->stream);  // M lives in host memory owned by the caller
+  // Mr is host memory of this frame: the copy must be done before it goes away
+  const cudaError_t es = cudaStreamSynchronize(op->stream);
+  return e != cudaSuccess ? e : es;
 }
 
 // CholeskyQR2 of every (frequency, instance) block of X, in place.

@@ -1,10 +1,11 @@
 // Per-frequency block algebra of the randomized SVD: Gram matrices of the
 // k-vector blocks and recombination of a block by a small matrix.  Products
 // are formed in the storage precision of the blocks; the Gram sums across
-// 256-point slabs and the small matrices are FP64.
+// 256-point slabs are FP64, and the small matrices are formed in FP64 on the
+// host and applied in the block's precision.
 //
 //   gram:    G[j][i][a][b] = sum_{p in instance i} conj(X[j][a][p]) X[j][b][p]
-//   combine: Out[j][b][p]  = sum_a In[j][a][p] M[j][inst(p)][a][b]
+//   combine: Out[j][b][p]  = sum_a In[j][a][p] M[j][inst(p)][a][b]   (M in the block's precision)
 //
 // gram gives the CholeskyQR factor (Q = X R^{-1}, R^H R = G) and the small
 // Hermitian eigenproblem W^H W = B B^H of the final SVD step.
@@ -76,13 +77,13 @@ __global__ void __launch_bounds__(256) gram_kernel(const cpx<R>* __restrict__ X,
 template <typename R>
 __global__ void __launch_bounds__(256) combine_kernel(const cpx<R>* In, int ka, int kb, int64_t n,
                                                      const int32_t* __restrict__ inst_of_point, int n_inst,
-                                                     const cpx<double>* __restrict__ M, cpx<R>* Out,
+                                                     const cpx<R>* __restrict__ M, cpx<R>* Out,
                                                      int64_t out_k) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (p >= n) return;
   const int inst = inst_of_point[p];
-  const cpx<double>* Mj = M + ((int64_t)j * n_inst + inst) * ka * kb;
+  const cpx<R>* Mj = M + ((int64_t)j * n_inst + inst) * ka * kb;
   // arithmetic in the element precision R (FP64 blocks: FP64; FP32 blocks: FP32)
   cpx<R> x[kMaxK];
 #pragma unroll
@@ -92,10 +93,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const cpx<R>* In, int ka, 
     cpx<R> s = mk<R>(0, 0);
 #pragma unroll
     for (int a = 0; a < kMaxK; ++a) {
-      if (a < ka) {
-        const cpx<double> m = Mj[a * kb + b];
-        cfma(s, x[a], mk<R>((R)m.re, (R)m.im));
-      }
+      if (a < ka) cfma(s, x[a], Mj[a * kb + b]);
     }
     Out[((int64_t)j * out_k + b) * n + p] = s;
   }
@@ -120,11 +118,11 @@ cudaError_t launch_gram(const void* X, int n_omega, int k, int64_t n, const int6
 
 template <typename R>
 cudaError_t launch_combine(const void* In, int n_omega, int ka, int kb, int64_t n, const int32_t* inst_of_point,
-                           int n_inst, const cpx<double>* M, void* Out, int64_t out_k, cudaStream_t st) {
+                           int n_inst, const void* M, void* Out, int64_t out_k, cudaStream_t st) {
   if (ka > kMaxK || kb > kMaxK) return cudaErrorInvalidValue;
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)n_omega);
-  combine_kernel<R><<<grid, 256, 0, st>>>((const cpx<R>*)In, ka, kb, n, inst_of_point, n_inst, M, (cpx<R>*)Out,
-                                          out_k);
+  combine_kernel<R><<<grid, 256, 0, st>>>((const cpx<R>*)In, ka, kb, n, inst_of_point, n_inst, (const cpx<R>*)M,
+                                          (cpx<R>*)Out, out_k);
   return cudaGetLastError();
 }
 
@@ -132,9 +130,9 @@ template cudaError_t launch_gram<double>(const void*, int, int, int64_t, const i
                                         cpx<double>*, cudaStream_t);
 template cudaError_t launch_gram<float>(const void*, int, int, int64_t, const int64_t*, int, int64_t, cpx<double>*,
                                        cudaStream_t);
-template cudaError_t launch_combine<double>(const void*, int, int, int, int64_t, const int32_t*, int,
-                                           const cpx<double>*, void*, int64_t, cudaStream_t);
-template cudaError_t launch_combine<float>(const void*, int, int, int, int64_t, const int32_t*, int,
-                                          const cpx<double>*, void*, int64_t, cudaStream_t);
+template cudaError_t launch_combine<double>(const void*, int, int, int, int64_t, const int32_t*, int, const void*,
+                                           void*, int64_t, cudaStream_t);
+template cudaError_t launch_combine<float>(const void*, int, int, int, int64_t, const int32_t*, int, const void*,
+                                          void*, int64_t, cudaStream_t);
 
 }  // namespace rsv

@@ -108,7 +108,7 @@ int march_tile_kernels(rsv_operator op, int steps, int kg) {
       return steps + 1;
     case RSV_OP_ADR2D: {
       const char* e = getenv("RSV_STENCIL_FUSED");
-      return (e != nullptr && e[0] == '0') ? 4 * steps + 1 : steps + 1;   // whole-step kernel by default
+      return (e != nullptr && e[0] == '1') ? steps + 1 : 4 * steps + 1;   // per-stage kernels by default
     }
     default:
       return 4 * steps + 1;

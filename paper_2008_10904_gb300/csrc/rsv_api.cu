@@ -224,7 +224,7 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
   if (op->kind == RSV_OP_GL1D) path = "cuda-core tile kernel";
   if (op->kind == RSV_OP_ADR2D) {
     const char* e = getenv("RSV_STENCIL_FUSED");
-    if (!(e != nullptr && e[0] == '0')) path = "cuda-core whole-step kernel";
+    if (e != nullptr && e[0] == '1') path = "cuda-core whole-step kernel";
   }
   if (op->kind == RSV_OP_DENSE) {
     if (op->prec == RSV_PREC_FP32 && op->tc_tiles[0] && !op->tc_disabled)

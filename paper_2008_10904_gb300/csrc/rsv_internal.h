@@ -232,6 +232,6 @@ cudaError_t launch_gram(const void* X, int n_omega, int k, int64_t n, const int6
 // Out[j][b][p] = sum_a In[j][a][p] * M[j][inst(p)][a][b] * colscale[j][inst][b]
 template <typename R>
 cudaError_t launch_combine(const void* In, int n_omega, int ka, int kb, int64_t n, const int32_t* inst_of_point,
-                           int n_inst, const cpx<double>* M, void* Out, int64_t out_k, cudaStream_t st);
+                           int n_inst, const void* M, void* Out, int64_t out_k, cudaStream_t st);   // M: cpx<R>
 
 }  // namespace rsv

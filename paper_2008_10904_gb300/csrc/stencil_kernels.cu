@@ -551,10 +551,12 @@ cudaError_t launch_adr2d_step(rsv_operator op, const StGeom& g, const R* uin, R*
   return cudaGetLastError();
 }
 
-// RSV_STENCIL_FUSED=0 selects the per-stage kernels (read at each march tile).
+// RSV_STENCIL_FUSED=1 selects the whole-step kernel (read at each march tile).  The
+// per-stage float4 kernels stay the default: on GB300 they measured 5% faster at the
+// 1024 x 512 x 16 workload although they move more bytes.
 bool adr2d_fused_enabled() {
   const char* e = getenv("RSV_STENCIL_FUSED");
-  return !(e != nullptr && e[0] == '0');
+  return e != nullptr && e[0] == '1';
 }
 
 template <typename R, int STAGE>
