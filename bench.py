@@ -299,6 +299,46 @@ def cpu_baseline(name: str, target_seconds: float = 15.0):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def subspace_angle_max(ma, mb, segs):
+    """Largest principal angle (radians) between span(ma[j, :, seg]) and span(mb[j, :, seg])."""
+    worst = 0.0
+    for j in range(ma.shape[0]):
+        for off, ln in segs:
+            qa, _ = np.linalg.qr(ma[j, :, off:off + ln].astype(np.complex128).T)
+            qb, _ = np.linalg.qr(mb[j, :, off:off + ln].T)
+            sv = np.linalg.svd(qa.conj().T @ qb, compute_uv=False)
+            worst = max(worst, float(np.arccos(np.clip(sv.min(), -1.0, 1.0))))
+    return worst
+
+
+def fp64_single_vector(w, dense, omega_dev, opts, stream, n_t):
+    """The plain comparator: the FP64 path marching one test vector (one direct march)."""
+    import torch
+    from paper_2008_10904_gb300 import rsv
+    steps = (w.n_transient_windows + 1) * n_t if w.variant == "ssrm" else n_t + w.tail_steps
+    cost = float(w.n) * w.n_omega * steps
+    if cost > 5e11:
+        return {"value": None, "unit": "actions/s",
+                "impl": "FP64 GPU march, one test vector", "note": "not run: its FP64 CUDA-core forcing synthesis "
+                f"alone would take tens of seconds ({cost:.1e} point-frequency-steps)"}
+    op64 = rsv.create_for_workload(w, rsv.RSV_PREC_FP64, stream=stream.cuda_stream, dense_matrix=dense)
+    x1 = omega_dev[:, :1, :].to(torch.complex128).contiguous()
+    y1 = torch.empty_like(x1)
+    ms = []
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rsv.rsv_march_direct(op64, x1, 1, y1, **opts)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    rsv.rsv_destroy_operator(op64)
+    return {"value": w.n_omega * n_instances(w) / (ms[-1] / 1e3), "unit": "actions/s",
+            "impl": "FP64 GPU march of one test vector (the library's FP64 path, k = 1), second of two runs",
+            "ms_per_march": ms[-1]}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -394,12 +434,22 @@ def run_ours(args):
     # accuracy: the timed path's gains against the FP64 path (itself parity-tested against the oracle)
     acc = None
     if prec_name != "fp64" and not args.skip_accuracy and dense is None and w.n * w.k * w.n_omega < 2 ** 27:
+        # response modes of both paths (untimed calls) for the subspace angle
+        m32 = torch.empty((w.n_omega, w.n_modes, w.n), dtype=torch.complex64, device="cuda")
+        g32 = np.zeros_like(gains)
+        rsv.rsv_gains_modes(op, omega_dev, w.k, w.n_power_iter, w.n_modes, g32, response_modes=m32, **opts)
         op64 = rsv.create_for_workload(w, rsv.RSV_PREC_FP64, stream=stream.cuda_stream, dense_matrix=dense)
         g64 = np.zeros_like(gains)
-        rsv.rsv_gains_modes(op64, omega_dev.to(torch.complex128), w.k, w.n_power_iter, w.n_modes, g64, **opts)
+        m64 = torch.empty((w.n_omega, w.n_modes, w.n), dtype=torch.complex128, device="cuda")
+        rsv.rsv_gains_modes(op64, omega_dev.to(torch.complex128), w.k, w.n_power_iter, w.n_modes, g64,
+                            response_modes=m64, **opts)
+        segs = [rsv.rsv_instance_range(op64, i) for i in range(ninst)]
         rsv.rsv_destroy_operator(op64)
         acc = {"gain_rel_err_max": float(np.max(np.abs(gains_timed - g64) / np.abs(g64))),
-               "vs": "FP64 GPU path (parity-tested against the FP64 oracle to 1e-10)"}
+               "subspace_angle_max_rad": subspace_angle_max(m32.cpu().numpy(), m64.cpu().numpy(), segs),
+               "vs": "FP64 GPU path (parity-tested against the FP64 oracle to 1e-10)",
+               "angle": f"largest principal angle between the leading-{w.n_modes} response-mode spans, "
+                        "over frequencies and instances"}
     elif prec_name == "fp64":
         acc = {"gain_rel_err_max": 0.0, "vs": "FP64 path itself (parity-tested against the oracle to 1e-10)"}
 
@@ -430,6 +480,8 @@ def run_ours(args):
         "accuracy": acc,
     }
     rsv.rsv_destroy_operator(op)
+    out["fp64_single_vector"] = (fp64_single_vector(w, dense, omega_dev, opts, stream, n_t)
+                                 if args.comparator else None)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             out["cpu_baseline"] = cpu_baseline(name)
@@ -478,6 +530,8 @@ def main(argv=None):
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--comparator", action="store_true",
+                    help="also time the FP64 path marching one test vector (two direct marches, untimed in value)")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     args = ap.parse_args(argv)
     if args.impl == "reference":

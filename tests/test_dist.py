@@ -53,3 +53,4 @@ def test_rank_blocks_are_independent():
     a = W.test_block(w, seed_offset=bench.rank_seed_offset(0))
     b = W.test_block(w, seed_offset=bench.rank_seed_offset(1))
     assert a.shape == b.shape and not np.allclose(a, b)
+
