@@ -499,8 +499,8 @@ def run_reference(args):
     name = args.workload
     w = workload(name)
     vals = []
-    for _ in range(args.warmup):
-        pass
+    for _ in range(args.warmup):          # untimed: the short probe march only
+        cpu_baseline(name, target_seconds=0.0)
     t0 = time.perf_counter()
     last = None
     for _ in range(max(1, args.steps)):
