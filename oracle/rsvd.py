@@ -14,7 +14,13 @@ B = U_s S V^H give gains S, response modes Q U_s and forcing modes V
 (Sec. 2.1: R_y = U Sigma V^H).
 
 `march_direct(block)` / `march_adjoint(block)` map [n_omega][k][n] blocks to
-[n_omega][k][n] blocks.  `instances` lists (offset, size) of independent
+[n_omega][k][n] blocks.
+
+Refinement (a higher-precision pass after a lower-precision rSVD): given the
+forcing basis Q of span V, one direct run gives R Q, and the SVD of R Q is the
+Rayleigh-Ritz step for R^H R on span(Q): the Ritz values are the gains of
+R restricted to that subspace, exact when span(Q) holds the leading right
+singular vectors and in error by O(eps^2) when the basis is off by eps.  `instances` lists (offset, size) of independent
 diagonal blocks of a batched operator; each gets its own QR and SVD.
 """
 from __future__ import annotations
@@ -86,6 +92,35 @@ def block_rsvd(march_direct, march_adjoint, omega_block, n_power_iter, n_modes,
             gains[i, j] = s[:n_modes]
             vi.append(vh[:n_modes].conj())                # forcing modes, rows
             ui.append((qj @ us[:, :n_modes]).T)           # response modes, rows
+        vmodes.append(np.array(vi))
+        umodes.append(np.array(ui))
+    return gains, vmodes, umodes
+
+
+def rayleigh_ritz_refine(march_direct, basis, n_modes, instances=None, real_rows=()):
+    """One direct run on an orthonormalised basis [n_omega][k][n] and the SVD of R Q.
+
+    Returns (gains [n_inst][n_omega][n_modes], forcing modes V, response modes U) as in
+    block_rsvd.  The adjoint run is not needed: R^H R restricted to span(Q) is
+    (R Q)^H (R Q), whose eigen-pairs are the singular pairs of R Q.
+    """
+    nom, kk, n = basis.shape
+    inst = instances or [(0, n)]
+    q = orthonormalize(basis, inst, real_rows)
+    y = march_direct(q)
+    gains = np.zeros((len(inst), nom, n_modes))
+    vmodes, umodes = [], []
+    for i, (off, size) in enumerate(inst):
+        vi, ui = [], []
+        for j in range(nom):
+            qj = q[j, :, off:off + size].T                # n x k
+            yj = y[j, :, off:off + size].T                # n x k = R Q
+            if j in real_rows:
+                yj = yj.real
+            us, s, wh = np.linalg.svd(yj, full_matrices=False)
+            gains[i, j] = s[:n_modes]
+            vi.append((qj @ wh.conj().T[:, :n_modes]).T)  # forcing modes Q W, rows
+            ui.append(us[:, :n_modes].T)                  # response modes, rows
         vmodes.append(np.array(vi))
         umodes.append(np.array(ui))
     return gains, vmodes, umodes

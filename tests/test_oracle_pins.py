@@ -169,6 +169,35 @@ def test_gains_approach_continuous_svd():
         assert np.allclose(gains[0, j], s[:2], rtol=1e-4)
 
 
+def test_rayleigh_ritz_refinement():
+    """A refinement pass (one direct run on the basis, SVD of R Q) returns the exact leading gains
+    when the basis spans the leading right singular vectors, and its error is quadratic in the
+    basis error (Rayleigh quotient), against the direct SVD of R_h."""
+    w, a, g = _small()
+    rm = [resolvent.rk4_discrete(a, om, g.h) for om in g.omegas]
+    svs = [np.linalg.svd(r) for r in rm]
+    k, n_modes = 4, 3
+    exact = np.array([s[:n_modes] for _, s, _ in svs])
+    vlead = np.stack([vh[:k].conj() for _, _, vh in svs])          # [n_omega][k][n]
+    direct = lambda b: _apply_r(rm, b)
+    g0, v0, u0 = rsvd.rayleigh_ritz_refine(direct, vlead, n_modes)
+    assert np.abs(g0[0] - exact).max() / exact.max() < 1e-12
+    # forcing modes: the right singular vectors up to phase
+    for j, (_, _, vh) in enumerate(svs):
+        for m in range(n_modes):
+            assert abs(abs(np.vdot(vh[m].conj(), v0[0][j][m])) - 1.0) < 1e-10
+    rng = np.random.default_rng(3)
+    errs = []
+    for eps in (1e-3, 1e-4):
+        noise = rng.standard_normal(vlead.shape) + 1j * rng.standard_normal(vlead.shape)
+        ge, _, _ = rsvd.rayleigh_ritz_refine(direct, vlead + eps * noise, n_modes)
+        errs.append(np.abs(ge[0] - exact).max() / exact.max())
+    assert errs[0] < 1e-3 and 50.0 < errs[0] / errs[1] < 200.0, errs   # tenfold eps -> hundredfold error
+    # through the oracle's march: the same numbers
+    gm, _, _ = rsvd.rayleigh_ritz_refine(lambda b: march.march(a, g, b, variant="ssrm", n_trans=12), vlead, n_modes)
+    assert np.abs(gm[0] - exact).max() / exact.max() < 1e-11
+
+
 def test_power_iteration_rate():
     """P7 / App. A: the gain estimate converges with error ratio (sigma2/sigma1)^2."""
     w, a, g = _small(n=16, n_omega=4, k=1, mu0=-0.3)
