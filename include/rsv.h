@@ -220,8 +220,12 @@ rsv_status rsv_profile_reset(rsv_operator op);
 rsv_status rsv_profile_read(rsv_operator op, int32_t category, int64_t* groups, int64_t* kernels, double* ms);
 
 /* One-line description of the operator's execution path (kernels chosen for
- * this GPU, e.g. the dense step's tensor-core variant and cluster capacity),
- * written NUL-terminated into buf (host, buflen bytes). */
+ * this GPU, e.g. the dense step's tensor-core variant and resident-CTA
+ * capacity) and of the latest march: "tile=" steps per time tile, "group="
+ * vectors marched together, "steps=" steps marched by its last vector group
+ * (smaller than the schedule when the TRM record was truncated by tail_tol).
+ * Written NUL-terminated into buf (host, buflen bytes); a longer description
+ * is cut at buflen - 1 characters.  Errors: INVALID_ARG. */
 rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen);
 
 /* Message of the calling thread's last failing call ("" if none). */
