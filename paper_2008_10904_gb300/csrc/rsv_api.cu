@@ -155,7 +155,7 @@ extern "C" rsv_status rsv_profile_read(rsv_operator op, int32_t category, int64_
 }
 
 extern "C" const char* rsv_last_error(void) { return g_err.c_str(); }
-extern "C" const char* rsv_version(void) { return "rsv 0.1 (sm_103a)"; }
+extern "C" const char* rsv_version(void) { return "rsv 0.2 (sm_103a)"; }
 
 extern "C" rsv_status rsv_create_operator(const rsv_operator_desc* d, void* stream, rsv_operator* out) {
   if (!d || !out) return fail(RSV_ERR_INVALID_ARG, "null argument");
