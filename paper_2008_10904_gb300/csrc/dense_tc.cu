@@ -489,11 +489,20 @@ __global__ void arrange_a_kernel(int n, int cs, const cpx<double>* __restrict__ 
 
 }  // namespace
 
+// Shapes of the tensor-core kernels: n a multiple of 128 with CS = n / 128 K slices, and
+// CS dividing the 64 rows of a row block (each of the CS CTAs of a row block owns
+// 64 / CS of its rows): CS in {1, 2, 4, 8}, n in {128, 256, 512, 1024}.  Other n take
+// the CUDA-core step.
+static bool tc_shape_ok(int n) {
+  if (n % kTileK != 0) return false;
+  const int cs = n / kTileK;
+  return cs >= 1 && cs <= 8 && kTileRows % cs == 0;
+}
+
 bool dense_tc_supported(rsv_operator op, int kg) {
   if (op->prec != RSV_PREC_FP32 || op->kind != RSV_OP_DENSE) return false;
   if (op->tc_disabled) return false;
-  const int n = (int)op->n;
-  if (n % kTileK != 0 || n / kTileK > 8 || kg > 32) return false;
+  if (!tc_shape_ok((int)op->n) || kg > 32) return false;
   return op->tc_tiles[0] != nullptr;
 }
 
@@ -504,7 +513,7 @@ size_t dense_tc_scratch_bytes(rsv_operator op) {
 // Build the hi/lo A tiles of D and D^H (after the FP64 propagator build).
 rsv_status dense_tc_prepare(rsv_operator op, const void* d64_direct) {
   const int n = (int)op->n;
-  if (op->prec != RSV_PREC_FP32 || n % kTileK != 0 || n / kTileK > 8 || op->tc_disabled) return RSV_OK;
+  if (op->prec != RSV_PREC_FP32 || !tc_shape_ok(n) || op->tc_disabled) return RSV_OK;
   const int cs = n / kTileK;
   const size_t floats = (size_t)(n / kTileRows) * cs * 2 * kATileFloats;
   for (int d = 0; d < 2; ++d) {

@@ -171,3 +171,21 @@ def test_dense_tensor_core_step(rsv, n, x_half, adjoint, path, k, monkeypatch):
         assert _relerr(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh, adjoint)) < TOL32_MARCH
     finally:
         rsv.rsv_destroy_operator(op)
+
+
+def test_dense_fp32_size_outside_tensor_tiles(rsv):
+    """n = 384: three 128-column K slices do not split a 64-row block evenly, so the FP32 path
+    takes the CUDA-core propagator step; it still matches the oracle."""
+    sysm = W.Dense(n=384, x_half_width=60.0)          # RK4 stable at dt = 0.01 (max |M| = 0.998)
+    w = W.Workload("dense_384", sysm, np.linspace(-1.0, 1.0, 8), 0.01, 3, "trm", tail_steps=2200)
+    a = W.hermite_gl_matrix(sysm)
+    op = rsv.create_for_workload(w, 1, dense_matrix=a)
+    try:
+        assert "cuda-core propagator step" in rsv.rsv_describe(op)
+        fh = W.test_block(w).astype(np.complex64).astype(np.complex128)
+        x = _dev(fh, 1)
+        y = x * 0
+        rsv.rsv_march_direct(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=200))
+        assert _relerr(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh)) < TOL32_MARCH
+    finally:
+        rsv.rsv_destroy_operator(op)
