@@ -14,6 +14,8 @@ Layout of the oracle, each module following the paper's statement:
   march        RK4 time march of the direct and adjoint systems with forcing
                synthesised from Fourier coefficients and a DFT of the response
                (Sec. 2.1 Eqs. (system)-(adsystemFreqDomain); TRM Sec. 2.2; SSRM Sec. 2.3 Eq. (forceFseries))
+  decay        unforced decay run of a seeded random state that sets the SSRM
+               transient length (Sec. 2.3); SplitMix64 counter-based initial state
   resolvent    closed forms: continuous R(w) = (i w I - A)^{-1} (Sec. 2.1) and
                the exact resolvent of the RK4-discretised system
   rsvd         power iteration with the gain estimate of App. A Eq. (tildeSig) and

@@ -224,3 +224,85 @@ def test_frequency_grid():
     assert g2.n_t == 80111 and g2.phi == 0.5
     with pytest.raises(ValueError):
         frequencies.make_grid(np.array([0.0, 0.1, 0.25]), 0.01)
+
+
+def _block_diag_rh(blocks, om, h):
+    """R_h(w) of each diagonal block of a block-diagonal system."""
+    return [resolvent.rk4_discrete(b, om, h) for b in blocks]
+
+
+def test_rsvd_instances_equal_blockwise_direct_svd():
+    """A batched (block-diagonal) system: with `instances`, each block gets its own QR and SVD,
+    so full-rank sketches (k = block size) give svd(R_h) of each block, modes up to phase."""
+    sysm = W.GL1D(n=(5, 5, 5), mu0=(-0.1, -0.3, 0.05), x0=-6.0, x1=6.0)
+    a = operators.gl1d(sysm)
+    blocks = [operators.gl1d(W.GL1D(n=(5,), mu0=(m,), x0=-6.0, x1=6.0)).toarray() for m in sysm.mu0]
+    g = frequencies.make_grid(np.linspace(-1.0, 1.0, 4), 0.05)
+    om_block = W.gaussian_block(17, 4, 5, 15)
+    md = lambda b: march.march(a, g, b, variant="ssrm", n_trans=30)
+    ma = lambda b: march.march(a, g, b, variant="ssrm", n_trans=30, adjoint=True)
+    inst = [(0, 5), (5, 5), (10, 5)]
+    gains, vm, um = rsvd.block_rsvd(md, ma, om_block, 1, 3, instances=inst)
+    for j, om in enumerate(g.omegas):
+        for i, rh in enumerate(_block_diag_rh(blocks, om, g.h)):
+            u, s, vh = np.linalg.svd(rh)
+            assert np.allclose(gains[i, j], s[:3], rtol=1e-10), (i, j)
+            for m in range(3):
+                assert abs(abs(np.vdot(vm[i][j][m], vh[m].conj())) - 1) < 1e-8
+                assert abs(abs(np.vdot(um[i][j][m], u[:, m])) - 1) < 1e-8
+    # the orthonormalised block is orthonormal within each instance and zero across
+    q = rsvd.orthonormalize(om_block, inst)
+    for j in range(4):
+        for off, size in inst:
+            blk = q[j, :, off:off + size]
+            assert np.allclose(blk @ blk.conj().T, np.eye(5), atol=1e-13)
+    # refinement on the same batch: per-block SVD of R Q
+    gr, _, _ = rsvd.rayleigh_ritz_refine(md, om_block, 3, instances=inst)
+    for j, om in enumerate(g.omegas):
+        for i, rh in enumerate(_block_diag_rh(blocks, om, g.h)):
+            assert np.allclose(gr[i, j], np.linalg.svd(rh, compute_uv=False)[:3], rtol=1e-10)
+
+
+def test_rsvd_real_rows_equal_real_zero_frequency_svd():
+    """A real system forced at w = 0: R_h(0) is a real matrix; with `real_rows` the rSVD of that
+    row works on real blocks and returns svd(R_h(0)) with real modes; the other rows are the
+    complex svd(R_h(w))."""
+    sysm = W.ADR2D(nx=4, ny=3, lx=4.0, ly=2.0, jet_delta=0.3, sponge_cells=1, visc=0.05)
+    a = operators.adr2d(sysm)
+    n = a.shape[0]
+    g = frequencies.make_grid(np.array([0.0, 0.5, 1.0, 1.5]), 0.05)
+    om_block = W.gaussian_block(23, 4, n, n, real_rows=[0])
+    kw = dict(variant="ssrm", n_trans=40, real_state=True)
+    md = lambda b: march.march(a, g, b, **kw)
+    ma = lambda b: march.march(a, g, b, adjoint=True, **kw)
+    gains, vm, um = rsvd.block_rsvd(md, ma, om_block, 0, 3, real_rows=[0])
+    for j, om in enumerate(g.omegas):
+        rh = resolvent.rk4_discrete(a, om, g.h)
+        if j == 0:
+            assert np.abs(rh.imag).max() < 1e-13 * np.abs(rh).max()
+            rh = rh.real
+        u, s, vh = np.linalg.svd(rh)
+        assert np.allclose(gains[0, j], s[:3], rtol=1e-10), j
+        for m in range(3):
+            assert abs(abs(np.vdot(vm[0][j][m], vh[m].conj())) - 1) < 1e-8
+            assert abs(abs(np.vdot(um[0][j][m], u[:, m])) - 1) < 1e-8
+    assert np.abs(np.asarray(vm[0][0]).imag).max() == 0.0 and np.abs(np.asarray(um[0][0]).imag).max() == 0.0
+    q = rsvd.orthonormalize(om_block, [(0, n)], real_rows=[0])
+    assert np.abs(q[0].imag).max() == 0.0 and np.allclose(q[0] @ q[0].T, np.eye(n), atol=1e-13)
+
+
+def test_trm_check_points_every_step_by_default():
+    """Sec. 2.2 ends the record once the norm is negligible and fixes no check cadence: the oracle
+    checks every step unless told otherwise.  A coarser cadence (the library checks at tile ends)
+    stops at or after the per-step stop, and both records are within tol of R_h fhat."""
+    w, a, g = _small()
+    fh = W.test_block(w)
+    ref = _apply_r([resolvent.rk4_discrete(a, om, g.h) for om in g.omegas], fh)
+    tol = 1e-6
+    y1, s1 = march.march(a, g, fh, variant="trm", tail_steps=20 * g.n_t, tail_tol=tol, return_steps=True)
+    y64, s64 = march.march(a, g, fh, variant="trm", tail_steps=20 * g.n_t, tail_tol=tol, check_every=64,
+                           return_steps=True)
+    assert g.n_t <= s1 <= s64 and s64 % 64 == 0 and s64 - s1 < 64 * 4
+    for y in (y1, y64):
+        assert np.abs(y - ref).max() / np.abs(ref).max() < tol
+    assert np.abs(y64 - y1).max() / np.abs(ref).max() < tol
