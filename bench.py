@@ -1,11 +1,21 @@
 #!/usr/bin/env python
-"""Benchmark: resolvent actions/s of the batched randomized-SVD time march.
+"""Benchmark: resolvent actions/s of the batched time march.
 
-One step = one full randomized SVD of the workload (every direct and adjoint
-march plus the per-frequency QR / SVD glue) through rsv_gains_modes.  One
-resolvent action = one test vector x one frequency through one march.
+Default step (--step march): one march of the whole workload, alternately
+direct and adjoint, followed by the CholeskyQR2 orthonormalisation of its
+Fourier block per frequency: one half-iteration of the block power
+iteration, so the step covers every stage of the method (twiddles,
+synthesis, RK4 operator stages, streaming DFT, schedule, per-frequency block
+algebra).  --step rsvd makes one step a whole randomized SVD through
+rsv_gains_modes.  One resolvent action = one test vector x one frequency
+through one march; a march step yields k x n_omega (x instances) actions.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c4] [--step march|rsvd]
+                  [--impl ours|reference]
+
+The default workload is the 3-D boundary-layer system (256 x 128 x 128 x 3
+state, 8 test vectors, 64 frequencies, steady-state method with three
+transient windows): the largest configuration that fits one GPU.
 
 Prints one JSON line (rank 0).  Under torchrun every rank marches its own
 independent copy of the workload (frequency / test-vector blocks are
@@ -34,9 +44,11 @@ import workloads as W  # noqa: E402
 
 METRIC = "resolvent actions/s (test vectors x freqs) at <=1e-4 gain error"
 L2_FLUSH_BYTES = 512 << 20
+ACC_FREQS = 4        # frequencies of the accuracy sample (the first ones of the grid)
+ACC_K = 3            # test vectors of the accuracy sample (= the leading gains compared)
 
 
-def marches_per_step(w) -> int:
+def marches_per_rsvd(w) -> int:
     return 2 * w.n_power_iter + 2
 
 
@@ -44,8 +56,16 @@ def n_instances(w) -> int:
     return len(w.system.n) if type(w.system).__name__ == "GL1D" else 1
 
 
-def actions_per_step(w) -> int:
-    return marches_per_step(w) * w.k * w.n_omega * n_instances(w)
+def actions_per_march(w) -> int:
+    return w.k * w.n_omega * n_instances(w)
+
+
+def actions_per_step(w, step_kind="march") -> int:
+    return actions_per_march(w) * (marches_per_rsvd(w) if step_kind == "rsvd" else 1)
+
+
+def steps_per_march(w, n_t) -> int:
+    return (w.n_transient_windows + 1) * n_t if w.variant == "ssrm" else n_t + w.tail_steps
 
 
 def workload(name: str):
@@ -54,6 +74,40 @@ def workload(name: str):
 
 def default_precision(name: str) -> str:
     return "fp64" if name == "c1" else "fp32"
+
+
+def big_block(w, k=None) -> bool:
+    return w.n * (k or w.k) * w.n_omega > (1 << 29)
+
+
+def sub_workload(w, omegas=None, k=None, n_power_iter=None):
+    """The workload with fewer frequencies (the first ones of its grid: same window and step) or vectors."""
+    return W.Workload(w.name, w.system, w.omegas if omegas is None else omegas, w.dt, k or w.k, w.variant,
+                      n_transient_windows=w.n_transient_windows, tail_steps=w.tail_steps,
+                      n_power_iter=w.n_power_iter if n_power_iter is None else n_power_iter, n_modes=w.n_modes,
+                      real_state=w.real_state, seed=w.seed)
+
+
+def seeded_block(w, k=None, seed_offset=0, dtype=None):
+    """A seeded test block [n_omega][k][n] on the device.
+
+    Small blocks are the workload's own (workloads.test_block, the inputs the oracle tests share).
+    Blocks above 2^24 entries are drawn on the device by torch's seeded generator with the same
+    distribution, (N(0,1) + i N(0,1)) / sqrt(2) per entry and a real N(0,1) row at w = 0 for
+    real-state systems: drawing tens of GB of Gaussians on the host takes minutes.
+    """
+    import torch
+    dtype = dtype or torch.complex64
+    kk = k or w.k
+    if w.n * kk * w.n_omega <= (1 << 24):
+        return torch.from_numpy(W.test_block(w, k=kk, seed_offset=seed_offset)).to(device="cuda", dtype=dtype)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(w.seed + seed_offset)
+    x = torch.randn((w.n_omega, kk, w.n), dtype=dtype, device="cuda", generator=g)   # re, im ~ N(0, 1/2)
+    for j, om in enumerate(w.omegas):
+        if w.real_state and om == 0.0:
+            x[j] = (x[j].real * math.sqrt(2.0)).to(dtype)
+    return x
 
 
 # ---------------------------------------------------------------------------
@@ -196,26 +250,27 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
     alu_peak = FP64_ALU_TFLOPS if prec == "fp64" else FP32_ALU_TFLOPS
     cflop = 4 if w.real_state else 8
     tc_contract = "contractions=tcgen05" in path
-    if cat in ("synthesis", "analysis") and tc_contract:
-        peak_tc = peaks["bf16_tflops"] * 1.1 / 2.25
+    # kernels timed inside a step of seconds: the sustained bf16 rate x the nominal TF32/bf16 ratio
+    peak_tc = peaks["bf16_tflops_sustained"] * 1.1 / 2.25
+    tc_src = "measured sustained bf16 x nominal tf32/bf16 ratio (1.1/2.25)"
     if cat == "synthesis":
         n_tau = S if dense else 2 * S + 1
         work = rows * w.n_omega * n_tau * cflop
         bound, unit, peak, per = "alu", "TFLOP/s", alu_peak, 1e12
         src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if prec != "fp64" else "nominal FP64"
         if tc_contract:
-            bound, peak, src = "tensor", peak_tc, "measured bf16 x nominal tf32/bf16 ratio (1.1/2.25)"
+            bound, peak, src = "tensor", peak_tc, tc_src
     elif cat == "analysis":
         work = rows * w.n_omega * S * cflop
         bound, unit, peak, per = "alu", "TFLOP/s", alu_peak, 1e12
         src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if prec != "fp64" else "nominal FP64"
         if tc_contract:
-            bound, peak, src = "tensor", peak_tc, "measured bf16 x nominal tf32/bf16 ratio (1.1/2.25)"
+            bound, peak, src = "tensor", peak_tc, tc_src
     elif cat == "march" and dense and "tcgen05" in path:
         work = 8.0 * w.n * w.n * w.k * S
-        peak = peaks["bf16_tflops"] * 1.1 / 2.25
+        peak = peak_tc
         bound, unit, per = "tensor", "TFLOP/s", 1e12
-        src = "measured bf16 x nominal tf32/bf16 ratio (1.1/2.25); 3xTF32 split products counted once"
+        src = tc_src + "; 3xTF32 split products counted once"
     elif cat == "march" and dense:
         work = 8.0 * w.n * w.n * w.k * S
         bound, unit, peak, per = "alu", "TFLOP/s", alu_peak, 1e12
@@ -240,11 +295,17 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the oracle on a bounded sample, in a subprocess with one thread
+# CPU baseline: the oracle on a bounded sample, in a subprocess
 # ---------------------------------------------------------------------------
+# The oracle marches k_s vectors for `steps` steps of the workload's schedule from the start;
+# its cost per step is proportional to the vectors it carries, so the full march of k vectors
+# is extrapolated as (seconds / steps) x steps_per_march x k / k_s.  Blocks too large for the
+# host (the 3-D workload) march one vector whose single seeded row serves every frequency
+# (the same work as distinct rows; drawing 64 rows of 12.6 M Gaussians would take a minute).
 CPU_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
+import numpy as np
 import workloads as W
 from oracle import frequencies, march, operators
 w = W.ALL[{name!r}]()
@@ -253,47 +314,71 @@ kind = type(w.system).__name__
 a = (W.hermite_gl_matrix(w.system) if kind == "Dense" else
      operators.gl1d(w.system) if kind == "GL1D" else
      operators.adr2d(w.system) if kind == "ADR2D" else operators.adv3d(w.system))
-fh = W.test_block(w)
+ks = {k_sample}
+if {one_row}:
+    row = W.test_block_row(w, 0, k=ks).astype(np.complex128)
+    if w.real_state:
+        row = row.real.astype(np.complex128)
+    fh = np.broadcast_to(row, (w.n_omega, ks, w.n))
+else:
+    fh = W.test_block(w, k=ks)
 total, first, forced = march.schedule(g, w.variant, w.n_transient_windows, w.tail_steps)
 steps = min({steps}, total)
-t0 = time.perf_counter()
-march.march(a, g, fh, variant=w.variant, n_trans=w.n_transient_windows, tail_steps=w.tail_steps,
-            real_state=w.real_state, stop_after=steps)
-dt = time.perf_counter() - t0
-print(json.dumps({{"seconds": dt, "steps": steps, "total_steps": int(total), "first": int(first)}}))
+secs = []
+for r in range({warmup} + {repeats}):
+    t0 = time.perf_counter()
+    march.march(a, g, fh, variant=w.variant, n_trans=w.n_transient_windows, tail_steps=w.tail_steps,
+                real_state=w.real_state, stop_after=steps if r >= {warmup} else 0)
+    secs.append(time.perf_counter() - t0)
+print(json.dumps({{"seconds": secs[-1], "samples": secs[{warmup}:], "steps": steps, "total_steps": int(total),
+                  "first": int(first)}}))
 """
 
 
-def cpu_baseline(name: str, target_seconds: float = 15.0):
-    w = workload(name)
-    if w.n * w.k * w.n_omega > (1 << 31):
-        return {"value": None, "unit": "actions/s", "cores": 1, "kind": "oracle",
-                "sample": f"not run: the FP64 oracle would hold {w.n * w.k * w.n_omega * 16 / 2**30:.0f} GiB "
-                          "of complex128 test block and accumulators on the host"}
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    big = w.n * w.k * w.n_omega > (1 << 28)
-    probe = 3 if big else (10 if type(w.system).__name__ in ("Dense", "ADV3D") else 100)
-    r = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, name=name, steps=probe)],
-                       capture_output=True, text=True, env=env, timeout=900)
+def _oracle_sample(name, steps, k_sample, one_row, threads, warmup=0, repeats=1):
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    r = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, name=name, steps=steps,
+                                                                 k_sample=k_sample, one_row=one_row,
+                                                                 warmup=warmup, repeats=repeats)],
+                       capture_output=True, text=True, env=env, timeout=3600)
     if r.returncode != 0:
-        return {"value": None, "error": r.stderr[-400:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
+        raise RuntimeError(r.stderr[-600:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(name: str, target_seconds: float = 15.0, warmup: int = 0, repeats: int = 1):
+    """The oracle, as it stands, on the host's cores (BLAS threads), on a bounded sample of one march.
+
+    A short probe sizes the sample to about target_seconds; with repeats > 1 the sample is timed
+    that many times in one process (after `warmup` untimed runs of the oracle's set-up path, no
+    steps) and `samples` lists each value.
+    """
+    w = workload(name)
+    cores = os.cpu_count() or 1
+    huge = w.n * w.k * w.n_omega > (1 << 28)
+    k_sample = 1 if huge else w.k
+    one_row = w.n * w.n_omega > (1 << 28)
+    probe = 1 if huge else (10 if type(w.system).__name__ in ("Dense", "ADV3D") else 100)
+    try:
+        steps = probe
+        if not huge:
+            d = _oracle_sample(name, probe, k_sample, one_row, cores)
+            steps = max(probe, min(d["total_steps"], int(target_seconds / (d["seconds"] / d["steps"]))))
+        d = _oracle_sample(name, steps, k_sample, one_row, cores, warmup, repeats)
+    except (RuntimeError, subprocess.TimeoutExpired) as e:
+        return {"value": None, "unit": "actions/s", "cores": cores, "kind": "oracle", "error": str(e)[-400:]}
     per_step = d["seconds"] / d["steps"]
-    steps = max(probe, min(d["total_steps"], int(target_seconds / per_step)))
-    if steps > probe:
-        r = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, name=name, steps=steps)],
-                           capture_output=True, text=True, env=env, timeout=900)
-        if r.returncode != 0:
-            return {"value": None, "error": r.stderr[-400:]}
-        d = json.loads(r.stdout.strip().splitlines()[-1])
-        per_step = d["seconds"] / d["steps"]
-    # one march = total_steps steps and yields k * n_omega (* instances) actions
-    march_s = per_step * d["total_steps"]
-    actions = w.k * w.n_omega * n_instances(w)
-    return {"value": actions / march_s, "unit": "actions/s", "cores": 1, "kind": "oracle",
-            "sample": f"{d['steps']} of the {d['total_steps']} steps of one direct march of {w.name} "
-                      f"(FP64 numpy oracle, one thread), extrapolated to the full march",
-            "seconds": d["seconds"]}
+    scale = d["total_steps"] * (w.k / k_sample) / d["steps"]
+    samples = [actions_per_march(w) / (t * scale) for t in d["samples"]]
+    march_s = per_step * d["total_steps"] * (w.k / k_sample)
+    sample = (f"{d['steps']} of the {d['total_steps']} steps of one direct march of {w.name} with "
+              f"{k_sample} of its {w.k} test vectors (FP64 numpy/scipy oracle, {cores} BLAS threads; sparse "
+              f"products single-threaded), extrapolated to the full march of all vectors")
+    if one_row:
+        sample += "; one seeded test-vector row serves every frequency (same work, fewer random draws)"
+    return {"value": actions_per_march(w) / march_s, "unit": "actions/s", "cores": cores, "kind": "oracle",
+            "sample": sample, "seconds": d["seconds"], "samples": samples}
 
 
 # ---------------------------------------------------------------------------
@@ -311,32 +396,80 @@ def subspace_angle_max(ma, mb, segs):
     return worst
 
 
-def fp64_single_vector(w, dense, omega_dev, opts, stream, n_t):
-    """The plain comparator: the FP64 path marching one test vector (one direct march)."""
+def accuracy_record(w, prec_name, dense, stream, rank):
+    """Gain accuracy of the timed precision on a bounded sample of the workload.
+
+    Sample: the full grid and schedule, the first ACC_FREQS frequencies (same window and step),
+    ACC_K test vectors, no power iteration (Y = R Omega, Q = qr(Y), W = R^H Q, svd).  The FP32
+    randomized SVD against the FP64 path's (itself parity-tested against the FP64 oracle to 1e-10)
+    on the same test vectors: the leading gains' largest relative difference and the largest
+    principal angle between the response-mode spans.
+    """
     import torch
     from paper_2008_10904_gb300 import rsv
-    steps = (w.n_transient_windows + 1) * n_t if w.variant == "ssrm" else n_t + w.tail_steps
-    cost = float(w.n) * w.n_omega * steps
-    if cost > 5e11:
-        return {"value": None, "unit": "actions/s",
-                "impl": "FP64 GPU march, one test vector", "note": "not run: its FP64 CUDA-core forcing synthesis "
-                f"alone would take tens of seconds ({cost:.1e} point-frequency-steps)"}
-    op64 = rsv.create_for_workload(w, rsv.RSV_PREC_FP64, stream=stream.cuda_stream, dense_matrix=dense)
-    x1 = omega_dev[:, :1, :].to(torch.complex128).contiguous()
+    if prec_name == "fp64":
+        return {"gain_rel_err_max": 0.0, "vs": "FP64 path itself (parity-tested against the oracle to 1e-10)"}
+    ws = sub_workload(w, omegas=w.omegas[:ACC_FREQS], k=ACC_K, n_power_iter=0)
+    nm, ninst = ACC_K, n_instances(ws)
+    x = seeded_block(ws, seed_offset=rank_seed_offset(rank), dtype=torch.complex128)
+    opts = rsv.march_opts_for(ws)
+    t0 = time.perf_counter()
+    res = {}
+    for prec, cdt in ((rsv.RSV_PREC_FP32, torch.complex64), (rsv.RSV_PREC_FP64, torch.complex128)):
+        op = rsv.create_for_workload(ws, prec, stream=stream.cuda_stream, dense_matrix=dense)
+        gains = np.zeros((ninst, ws.n_omega, nm))
+        modes = torch.empty((ws.n_omega, nm, ws.n), dtype=cdt, device="cuda")
+        rsv.rsv_gains_modes(op, x.to(cdt), ws.k, ws.n_power_iter, nm, gains, response_modes=modes, **opts)
+        segs = [rsv.rsv_instance_range(op, i) for i in range(ninst)]
+        rsv.rsv_destroy_operator(op)
+        res[prec] = (gains, modes.cpu().numpy())
+        del modes
+    del x
+    torch.cuda.empty_cache()
+    g32, m32 = res[rsv.RSV_PREC_FP32]
+    g64, m64 = res[rsv.RSV_PREC_FP64]
+    return {"gain_rel_err_max": float(np.max(np.abs(g32 - g64) / np.abs(g64))),
+            "subspace_angle_max_rad": subspace_angle_max(m32, m64, segs),
+            "vs": "FP64 GPU path (parity-tested against the FP64 oracle to 1e-10), same test vectors",
+            "sample": f"full grid and schedule, first {ws.n_omega} frequencies, {ws.k} test vectors, no power "
+                      f"iteration, leading {nm} gains",
+            "angle": f"largest principal angle between the leading-{nm} response-mode spans, over frequencies "
+                     "and instances",
+            "seconds": time.perf_counter() - t0}
+
+
+def fp64_single_vector(w, dense, stream, n_t, rank):
+    """The plain comparator: the library's FP64 path marching one test vector for all frequencies.
+
+    Timed over one window of N_T steps (forced and analysed: SSRM with no transient window), the
+    second of two runs, and scaled to the workload's steps per march.
+    """
+    import torch
+    from paper_2008_10904_gb300 import rsv
+    w1 = sub_workload(w, k=1)
+    try:
+        op64 = rsv.create_for_workload(w1, rsv.RSV_PREC_FP64, stream=stream.cuda_stream, dense_matrix=dense)
+    except rsv.RsvError as e:
+        return {"value": None, "note": f"not run: {e}"}
+    x1 = seeded_block(w1, seed_offset=rank_seed_offset(rank), dtype=torch.complex128)
     y1 = torch.empty_like(x1)
     ms = []
     for _ in range(2):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rsv.rsv_march_direct(op64, x1, 1, y1, **opts)
+        rsv.rsv_march_direct(op64, x1, 1, y1, variant="ssrm", n_transient_windows=0)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     rsv.rsv_destroy_operator(op64)
-    return {"value": w.n_omega * n_instances(w) / (ms[-1] / 1e3), "unit": "actions/s",
-            "impl": "FP64 GPU march of one test vector (the library's FP64 path, k = 1), second of two runs",
-            "ms_per_march": ms[-1]}
+    del x1, y1
+    torch.cuda.empty_cache()
+    per_march_ms = ms[-1] * steps_per_march(w, n_t) / n_t
+    return {"value": w.n_omega * n_instances(w) / (per_march_ms / 1e3), "unit": "actions/s",
+            "impl": "FP64 GPU march of one test vector (the library's FP64 path, k = 1)",
+            "sample": f"one window of {n_t} steps (second of two runs), scaled to {steps_per_march(w, n_t)} steps",
+            "ms_per_march": per_march_ms}
 
 
 def run_ours(args):
@@ -364,24 +497,31 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     op = rsv.create_for_workload(w, prec, stream=stream.cuda_stream, dense_matrix=dense)
     n_t, h = rsv.rsv_set_frequencies(op, w.omegas)
-    path = rsv.rsv_describe(op)
     opts = rsv.march_opts_for(w, tile_steps=args.tile)
-    big = w.n * w.k * w.n_omega > (1 << 29)
-    if big:   # draw per frequency row straight into a pinned host block (no full complex128 copy)
-        pinned = torch.empty((w.n_omega, w.k, w.n), dtype=torch.complex64, pin_memory=True)
-        for j in range(w.n_omega):
-            pinned[j].copy_(torch.from_numpy(W.test_block_row(w, j, seed_offset=rank_seed_offset(rank))))
-        omega_dev = pinned.to(device="cuda", dtype=cdt)
-    else:
-        omega_host = W.test_block(w, seed_offset=rank_seed_offset(rank))
-        omega_dev = torch.from_numpy(omega_host).to(device="cuda", dtype=cdt)
-        pinned = torch.from_numpy(omega_host.astype(np.complex128 if prec_name == "fp64" else np.complex64)).pin_memory()
+    # the seeded test block, resident on the device and pinned on the host for the end-to-end runs
+    x0 = seeded_block(w, seed_offset=rank_seed_offset(rank), dtype=cdt)
+    pinned = torch.empty((w.n_omega, w.k, w.n), dtype=cdt, pin_memory=True)
+    pinned.copy_(x0)
+    bufs = [x0, None]
     ninst = n_instances(w)
+    step_kind = args.step
+    if step_kind == "march":
+        bufs[1] = torch.empty_like(bufs[0])
+        rfac = np.zeros((w.n_omega, ninst, w.k, w.k), dtype=np.complex128)
     gains = np.zeros((ninst, w.n_omega, w.n_modes))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    counter = [0]
 
-    def step():
-        rsv.rsv_gains_modes(op, omega_dev, w.k, w.n_power_iter, w.n_modes, gains, **opts)
+    def step(read_r=False):
+        """One step; read_r: also bring the step's result (R factors / gains) to the host."""
+        if step_kind == "rsvd":
+            rsv.rsv_gains_modes(op, bufs[0], w.k, w.n_power_iter, w.n_modes, gains, **opts)
+            return
+        i = counter[0]
+        src, dst = bufs[i % 2], bufs[(i + 1) % 2]
+        (rsv.rsv_march_adjoint if i % 2 else rsv.rsv_march_direct)(op, src, w.k, dst, **opts)
+        rsv.rsv_orthonormalize(op, dst, w.k, rfac if read_r else None)
+        counter[0] += 1
 
     for _ in range(args.warmup):
         step()
@@ -411,80 +551,66 @@ def run_ours(args):
     clocks = sampler.stop()
     prof = {c: rsv.rsv_profile_read(op, i) for i, c in enumerate(rsv.PROFILE_CATEGORIES)}  # (groups, kernels, ms)
     sec_max = max_over_ranks(total_ms / 1e3, device="cuda")
-    value = job_throughput(actions_per_step(w) * args.steps, ws, sec_max)
-    gains_timed = gains.copy()
+    value = job_throughput(actions_per_step(w, step_kind) * args.steps, ws, sec_max)
+    path = rsv.rsv_describe(op)   # includes the tile / group sizes the marches used
 
-    # end to end through the public API: pinned host test block in, gains on the host out
+    # end to end through the public API: each step copies its input block from pinned host memory
+    # and reads its result back (march step: the R factors of the orthonormalisation; rSVD: gains)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     h2d = pinned.numel() * pinned.element_size()
-    d2h = gains.nbytes
+    d2h = rfac.nbytes if step_kind == "march" else gains.nbytes
     e2e_ms = 0.0
-    for _ in range(max(1, args.steps)):
+    for _ in range(e2e_steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        omega_dev.copy_(pinned, non_blocking=True)
-        step()
+        tgt = bufs[0] if step_kind == "rsvd" else bufs[counter[0] % 2]
+        tgt.copy_(pinned, non_blocking=True)
+        step(read_r=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     e2e_sec = max_over_ranks(e2e_ms / 1e3, device="cuda")
-    e2e_value = job_throughput(actions_per_step(w) * max(1, args.steps), ws, e2e_sec)
+    e2e_value = job_throughput(actions_per_step(w, step_kind) * e2e_steps, ws, e2e_sec)
+    rsv.rsv_destroy_operator(op)
+    del bufs, flush, pinned
+    torch.cuda.empty_cache()
 
-    # accuracy: the timed path's gains against the FP64 path (itself parity-tested against the oracle)
-    acc = None
-    if prec_name != "fp64" and not args.skip_accuracy and dense is None and w.n * w.k * w.n_omega < 2 ** 27:
-        # response modes of both paths (untimed calls) for the subspace angle
-        m32 = torch.empty((w.n_omega, w.n_modes, w.n), dtype=torch.complex64, device="cuda")
-        g32 = np.zeros_like(gains)
-        rsv.rsv_gains_modes(op, omega_dev, w.k, w.n_power_iter, w.n_modes, g32, response_modes=m32, **opts)
-        op64 = rsv.create_for_workload(w, rsv.RSV_PREC_FP64, stream=stream.cuda_stream, dense_matrix=dense)
-        g64 = np.zeros_like(gains)
-        m64 = torch.empty((w.n_omega, w.n_modes, w.n), dtype=torch.complex128, device="cuda")
-        rsv.rsv_gains_modes(op64, omega_dev.to(torch.complex128), w.k, w.n_power_iter, w.n_modes, g64,
-                            response_modes=m64, **opts)
-        segs = [rsv.rsv_instance_range(op64, i) for i in range(ninst)]
-        rsv.rsv_destroy_operator(op64)
-        acc = {"gain_rel_err_max": float(np.max(np.abs(gains_timed - g64) / np.abs(g64))),
-               "subspace_angle_max_rad": subspace_angle_max(m32.cpu().numpy(), m64.cpu().numpy(), segs),
-               "vs": "FP64 GPU path (parity-tested against the FP64 oracle to 1e-10)",
-               "angle": f"largest principal angle between the leading-{w.n_modes} response-mode spans, "
-                        "over frequencies and instances"}
-    elif prec_name == "fp64":
-        acc = {"gain_rel_err_max": 0.0, "vs": "FP64 path itself (parity-tested against the oracle to 1e-10)"}
-
-    path = rsv.rsv_describe(op)   # now includes the tile / group sizes the marches used
     dom = max(prof, key=lambda c: prof[c][2])
     desc = dict(kv.split("=", 1) for kv in path.split() if "=" in kv)
     tile = int(desc.get("tile", args.tile or 256))
     rows = int(desc.get("group", w.k)) * w.n
     roof = kernel_model(dom, w, prec_name, tile, prof[dom][0], prof[dom][2], rows, path)
     launches = sum(v[1] for v in prof.values())
-    steps_per_march = {"ssrm": (w.n_transient_windows + 1) * n_t, "trm": n_t + w.tail_steps}[w.variant]
+    acc = None if args.skip_accuracy else accuracy_record(w, prec_name, dense, stream, rank)
+    comp = None if args.no_comparator else fp64_single_vector(w, dense, stream, n_t, rank)
     out = {
         "metric": METRIC, "value": value, "unit": "actions/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec_name == "fp64" else "f32",
         "data": "synthetic (seeded Gaussian test vectors, workload of the config)",
         "config": {"workload": w.name, "n": w.n, "k": w.k, "n_omega": w.n_omega, "variant": w.variant,
-                   "steps_per_window": n_t, "h": h, "steps_per_march": steps_per_march,
-                   "marches_per_step": marches_per_step(w), "actions_per_step": actions_per_step(w),
+                   "steps_per_window": n_t, "h": h, "steps_per_march": steps_per_march(w, n_t),
+                   "step": ("one march (alternately direct and adjoint) + CholeskyQR2 of its block per "
+                            "frequency: half an iteration of the block power iteration"
+                            if step_kind == "march" else "one randomized SVD (all marches + glue)"),
+                   "actions_per_step": actions_per_step(w, step_kind),
                    "power_iterations": w.n_power_iter, "precision": prec_name,
-                   "l2": "flushed between steps (512 MiB write outside the timed events)",
+                   "l2": "flushed between steps (512 MiB write outside the timed events); state blocks exceed L2",
                    "parallelism": f"independent replicas x{ws}", "path": path},
-        "e2e": {"value": e2e_value, "unit": "actions/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "actions/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
         "gpu_launches": launches,
         "kernel_ms": {c: {"groups": v[0], "kernels": v[1], "ms": v[2]} for c, v in prof.items()},
         "roofline": roof,
         "clocks": clocks,
         "accuracy": acc,
+        "fp64_single_vector": comp,
     }
-    rsv.rsv_destroy_operator(op)
-    out["fp64_single_vector"] = (fp64_single_vector(w, dense, omega_dev, opts, stream, n_t)
-                                 if args.comparator else None)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
-            out["cpu_baseline"] = cpu_baseline(name)
+            out["cpu_baseline"] = cpu_baseline(name, target_seconds=args.ref_seconds)
         else:
             out["cpu_baseline"] = None
         print(json.dumps(out), flush=True)
@@ -493,21 +619,16 @@ def run_ours(args):
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample of one march of the workload."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     name = args.workload
     w = workload(name)
-    vals = []
-    for _ in range(args.warmup):          # untimed: the short probe march only
-        cpu_baseline(name, target_seconds=0.0)
     t0 = time.perf_counter()
-    last = None
-    for _ in range(max(1, args.steps)):
-        last = cpu_baseline(name, target_seconds=args.ref_seconds)
-        if last.get("value"):
-            vals.append(last["value"])
+    last = cpu_baseline(name, target_seconds=args.ref_seconds, warmup=args.warmup, repeats=max(1, args.steps))
     wall = time.perf_counter() - t0
+    vals = last.get("samples") or []
     v = statistics.median(vals) if vals else None
     out = {"metric": METRIC, "value": v, "unit": "actions/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps), "higher_is_better": True,
@@ -525,13 +646,15 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(W.ALL), default="c2")
+    ap.add_argument("--workload", choices=sorted(W.ALL), default="c4")
+    ap.add_argument("--step", choices=["march", "rsvd"], default="march")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default=None)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement (<= --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
-    ap.add_argument("--comparator", action="store_true",
-                    help="also time the FP64 path marching one test vector (two direct marches, untimed in value)")
+    ap.add_argument("--no-comparator", action="store_true",
+                    help="skip the FP64 one-test-vector comparator (one window, scaled to a march)")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     args = ap.parse_args(argv)
     if args.impl == "reference":

@@ -2,7 +2,7 @@
  * rsv.h - C ABI of the GB300 resolvent time-march library (librsv.so).
  *
  * The library computes the action of the resolvent of a stable linear system
- *     du/dt = A u + f(t),   y = u                       (B = C = I)
+ *     du/dt = A u + B f(t),   y = C u      (B, C diagonal; B = C = I by default)
  * on Fourier coefficients for many frequencies at once by time marching,
  * and the resolvent gains and modes from it (Martini, Rodriguez, Towne &
  * Cavalieri, "Efficient computation of global resolvent modes", Sec. 2).
@@ -106,7 +106,14 @@ typedef struct {
 
 typedef struct {
   int32_t variant;              /* rsv_variant                                      */
-  int32_t n_transient_windows;  /* SSRM: forced windows before the analysed one     */
+  int32_t n_transient_windows;  /* SSRM: forced windows before the analysed one;
+                                   -1 = as many as the decay run of rsv_decay_probe
+                                   needs (Sec. 2.3): ceil(decay steps / N_T), with
+                                   decay_tol / decay_max_steps / decay_seed below,
+                                   check points every tile_steps steps; the run is
+                                   made once per operator, direction and setting and
+                                   remembered until the frequencies change.  A probe
+                                   that grows or does not decay: RSV_ERR_UNSTABLE.  */
   int64_t tail_steps;           /* TRM: unforced steps after the forcing window
                                    (the cap on the tail when tail_tol > 0)          */
   int32_t tile_steps;           /* steps per time tile S (0 = library default)      */
@@ -124,6 +131,12 @@ typedef struct {
                                    ends: multiples of the tile length reported by
                                    rsv_describe ("tile="), and the last step.  SSRM
                                    ignores it.  Negative or NaN: INVALID_ARG.       */
+  double decay_tol;             /* n_transient_windows = -1: the probe's norm ratio
+                                   target (0 = 1e-8)                                 */
+  int64_t decay_max_steps;      /* n_transient_windows = -1: cap on the probe's steps
+                                   (0 = 1000 windows of N_T steps)                   */
+  uint64_t decay_seed;          /* n_transient_windows = -1: SplitMix64 stream of the
+                                   probe's random initial state                     */
 } rsv_march_opts;
 
 /* Create an operator.  desc: system description (read during the call only).
@@ -151,6 +164,22 @@ rsv_status rsv_instance_range(rsv_operator op, int32_t i, int64_t* offset, int64
 rsv_status rsv_set_frequencies(rsv_operator op, const double* omega, int32_t n_omega, double dw,
                                int64_t* n_steps_per_window, double* h);
 
+/* Forcing matrix B, observation matrix C and the metrics of the forcing and
+ * observation spaces (Sec. 2.1: y = C u, the inner products <a, b>_W = a^H W b
+ * and the adjoints B^dag = W_f^{-1} B^H W_u, C^dag = W_y^{-1} C^H W_u), all
+ * diagonal over the state: host arrays of n doubles (read during the call),
+ * NULL = identity; all four NULL clears them.  b, c >= 0 (masks or weights in
+ * space), w_f, w_y > 0 (e.g. quadrature weights).  Afterwards
+ *   rsv_march_direct  returns y_hat = C R_h B f_hat,
+ *   rsv_march_adjoint returns w_hat = R_y^dag y_hat = W_f^{-1} B^H R_h^H C^H W_y y_hat
+ *                     (the state metric W_u cancels from the adjoint run's output),
+ *   rsv_gains_modes / rsv_refine_gains work on W_y^{1/2} C R_h B W_f^{-1/2}: gains
+ *   ||y||_{W_y} / ||f||_{W_f}, forcing modes unit in W_f, response modes unit in
+ *   W_y (the refinement basis is W_f-orthonormalised);
+ * rsv_orthonormalize stays Euclidean.  Errors: INVALID_ARG (negative,
+ * non-finite or zero metric entries), OOM, CUDA. */
+rsv_status rsv_set_weights(rsv_operator op, const double* b, const double* c, const double* w_f, const double* w_y);
+
 /* Direct run (Sec. 2.1 Eq. (system), methods of Sec. 2.2 / 2.3): march
  * du/dt = A u + f(t) from u = 0 with f synthesised from f_hat, and return the
  * response's Fourier coefficients y_hat = R_h(w_j) f_hat_j, where R_h is the
@@ -171,23 +200,45 @@ rsv_status rsv_march_adjoint(rsv_operator op, const void* y_hat, int32_t k, cons
 
 /* rsv_march_direct without any device allocation.  The paper has no
  * counterpart: this is a service to callers that cannot allocate device
- * memory once running - a host solver that gives the library a fixed memory
- * budget at start-up, a thread recording into a CUDA stream capture, a
- * real-time loop that must not wait on the allocator.  rsv_march_direct
- * grows the operator's workspace on demand; this entry point instead keeps
- * the march's scratch (state, forcing and snapshot tiles, FP64
- * accumulators) in one static device array of RSV_STATIC_SCRATCH_BYTES that
- * every GPU loading the library holds until the process exits.  Arguments
- * and result are those of rsv_march_direct (same y_hat to rounding).  The
- * tile length is halved until the scratch fits; if it cannot fit,
- * RSV_ERR_INVALID_ARG names the bytes needed.  All calls share the array and
- * each clears what must start at zero; calls whose device work overlaps
- * race on it.  The first call on a device takes the array's device address
- * (cudaGetSymbolAddress) with that device current: make it before any stream
- * capture begins.  The operator and its frequencies must already exist
- * (rsv_create_operator / rsv_set_frequencies allocate). */
+ * memory once running - a host solver that reserves the whole device-memory
+ * budget for its own pool at start-up and forbids any later cudaMalloc, or a
+ * real-time loop that must never stall on the allocator (cudaMalloc and
+ * cudaFree can synchronise the device).  rsv_march_direct grows the
+ * operator's workspace on demand; this entry point instead keeps the march's
+ * scratch (state, forcing and snapshot tiles, FP64 accumulators) in one
+ * static device array of RSV_STATIC_SCRATCH_BYTES that every GPU loading the
+ * library holds until the process exits.  Arguments and result are those of
+ * rsv_march_direct (same y_hat to rounding) for the GL1D kind; TRM runs its
+ * whole tail (tail_tol must be 0).  The tile length is halved until the
+ * scratch fits; if it cannot fit, RSV_ERR_INVALID_ARG names the bytes
+ * needed.  All calls share the array and each clears what must start at
+ * zero; calls whose device work overlaps race on it.  Like every other
+ * entry point the call ends by synchronising the operator's stream.  The
+ * first call on a device takes the array's device address
+ * (cudaGetSymbolAddress) with that device current: make it before any
+ * stream capture begins.  The operator and its frequencies must already
+ * exist (rsv_create_operator / rsv_set_frequencies allocate). */
 rsv_status rsv_march_direct_static(rsv_operator op, const void* f_hat, int32_t k, const rsv_march_opts* opts,
                                    void* y_hat);
+
+/* Decay run (Sec. 2.3: the transient length of the steady-state method is
+ * estimated from a prior run in which the norm of a random initial condition
+ * falls to a prescribed small value).  Marches the unforced system
+ * du/dt = A u (adjoint = 1: A^H) with the operator's step h from the random
+ * state u_0 whose entries are uniform in [-1, 1): value i of the SplitMix64
+ * stream `seed` (Steele, Lea & Flood 2014; increment 0x9E3779B97F4A7C15),
+ * top 53 bits as 2 (z >> 11) 2^-53 - 1; a complex state takes values 2p and
+ * 2p + 1 as the real and imaginary parts of entry p, a real state value p.
+ * Every check_every steps (0 = the default tile length) it takes, per
+ * instance, ||u_i|| / ||u_0,i|| and stops at the first check point where the
+ * largest of them is <= tol.  Outputs (host, nullable): *steps marched and
+ * *ratio (largest instance ratio) there.  Errors: RSV_ERR_UNSTABLE when a
+ * ratio exceeds 1e6 or turns non-finite at a check point (the system grows),
+ * or when max_steps pass without decay (outputs still written);
+ * INVALID_ARG (tol not in (0, 1), max_steps < 1); STATE (no frequencies:
+ * h is set by rsv_set_frequencies). */
+rsv_status rsv_decay_probe(rsv_operator op, int32_t adjoint, double tol, int64_t max_steps, uint64_t seed,
+                           int32_t check_every, int64_t* steps, double* ratio);
 
 /* Randomized SVD of R_h(w_j) for every frequency (Sec. 1 cites it; App. A for
  * the power iteration it generalises): Y = R Omega, n_power_iter times
@@ -201,6 +252,48 @@ rsv_status rsv_march_direct_static(rsv_operator op, const void* f_hat, int32_t k
 rsv_status rsv_gains_modes(rsv_operator op, const void* omega_block, int32_t k, int32_t n_power_iter,
                            int32_t n_modes, const rsv_march_opts* opts, double* gains, void* forcing_modes,
                            void* response_modes);
+
+/* Rayleigh-Ritz refinement on a given forcing basis (App. A: gains and modes
+ * estimated from the eigen-decomposition of R^H R projected onto a subspace).
+ * With Q the orthonormalised basis (CholeskyQR2 per frequency and instance),
+ * one direct run gives Y = R Q, and the eigen-decomposition of
+ * Y^H Y = Q^H R^H R Q = W S^2 W^H yields gains S (descending), forcing modes
+ * Q W and response modes Y W S^{-1}.  Made on an RSV_PREC_FP64 operator with
+ * the basis of a lower-precision randomized SVD (its forcing modes, n_modes
+ * = k), this is the FP64 refinement pass: the gain error becomes quadratic in
+ * the basis error.  basis: device [n_omega][k][n] of the operator's element
+ * type (read only; for real-state kinds the w = 0 row must be real, its
+ * imaginary part is ignored).  gains: HOST [n_instances][n_omega][n_modes];
+ * forcing_modes / response_modes: DEVICE [n_omega][n_modes][n] (nullable).
+ * n_modes <= k <= 32, k <= every instance's length.  Errors: INVALID_ARG,
+ * STATE, DIVERGED (basis loses rank), and those of the march. */
+rsv_status rsv_refine_gains(rsv_operator op, const void* basis, int32_t k, int32_t n_modes,
+                            const rsv_march_opts* opts, double* gains, void* forcing_modes, void* response_modes);
+
+/* Optimal and suboptimal gains by the Arnoldi algorithm (App. A: the runs give
+ * w = R^H R f; each new forcing f_{n+1} is the part of w_n orthogonal to
+ * f_0 .. f_n, Eq. (freqOrt); the projection H = F^H W of R^H R on the
+ * orthonormal Krylov basis F is Hermitian tridiagonal, and H psi = gamma^2 psi
+ * gives gains gamma, forcing modes F psi and response modes R F psi / gamma).
+ * One vector per frequency and instance, m iterations = m direct + m adjoint
+ * runs; classical Gram-Schmidt with one reorthogonalisation.  f0: device
+ * [n_omega][1][n] start vectors of the operator's element type (for real-state
+ * kinds the w = 0 row must be real).  gains: HOST [n_instances][n_omega][n_modes]
+ * descending; forcing_modes / response_modes: DEVICE [n_omega][n_modes][n]
+ * (nullable), unit norm (in W_f / W_y with rsv_set_weights).  1 <= n_modes <= m
+ * <= 31, m <= every instance's length.  Errors: INVALID_ARG, STATE, DIVERGED
+ * (the Krylov space stopped growing), and those of the march. */
+rsv_status rsv_arnoldi_gains(rsv_operator op, const void* f0, int32_t m, int32_t n_modes,
+                             const rsv_march_opts* opts, double* gains, void* forcing_modes, void* response_modes);
+
+/* Orthonormalise a block in place, per frequency and instance (CholeskyQR2:
+ * the QR factorisation with a positive real diagonal in R; the per-frequency
+ * normalisation and orthogonalisation of Fourier blocks of Sec. 2.3).
+ * block: device [n_omega][k][n] of the operator's element type.  r_factor:
+ * HOST [n_omega][n_instances][k][k] complex128 (re, im) row-major, upper
+ * triangular, block = Q R (nullable).  Errors: INVALID_ARG, STATE, DIVERGED
+ * (a block is rank deficient). */
+rsv_status rsv_orthonormalize(rsv_operator op, void* block, int32_t k, double* r_factor);
 
 /* y = A x (adjoint = 0) or y = A^H x (adjoint = 1) for a device block x, y [k][n]
  * of the operator's element type (complex for every kind; real-state kinds

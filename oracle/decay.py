@@ -68,21 +68,25 @@ def initial_state(n: int, seed: int, complex_state: bool) -> np.ndarray:
 
 
 def decay_probe(a, h: float, u0, tol: float, max_steps: int, check_every: int = 1,
-                growth_limit: float = 1e6):
+                growth_limit: float = 1e6, instances=None):
     """Unforced RK4 march from u0 with step h until ||u|| <= tol ||u0|| at a check point.
 
-    Returns (steps, ratio, status): steps marched, ||u|| / ||u0|| there, and
+    `instances` lists (offset, size) of the independent diagonal blocks of a
+    batched system; the ratio is then the largest of the blocks' own ratios
+    ||u_i|| / ||u0_i|| (every block must have decayed).
+    Returns (steps, ratio, status): steps marched, the ratio there, and
     status "decayed", "grew" (ratio above growth_limit or non-finite at a check
     point) or "cap" (max_steps marched without either).
     """
     u = np.array(u0).reshape(-1, 1)
-    n0 = float(np.linalg.norm(u))
+    segs = instances or [(0, u.shape[0])]
+    n0 = [float(np.linalg.norm(u[o:o + s])) for o, s in segs]
     zero = np.zeros_like(u)
     ratio = 1.0
     for step in range(1, max_steps + 1):
         u = _march.rk4_step(a, u, h, zero, zero, zero)
         if step % check_every == 0 or step == max_steps:
-            ratio = float(np.linalg.norm(u)) / n0
+            ratio = max(float(np.linalg.norm(u[o:o + s])) / n for (o, s), n in zip(segs, n0))
             if not math.isfinite(ratio) or ratio > growth_limit:
                 return step, ratio, "grew"
             if ratio <= tol:

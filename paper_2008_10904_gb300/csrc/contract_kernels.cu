@@ -184,12 +184,26 @@ __global__ void __launch_bounds__(kTPB) analysis_kernel(TileGeom g, const void* 
 
 template <typename R>
 __global__ void finish_kernel(const cpx<double>* __restrict__ acc, int64_t acc_stride, int n_omega, int64_t rows,
-                              double scale, cpx<R>* __restrict__ out, int64_t out_stride) {
+                              double scale, const double* __restrict__ pscale, int64_t n, cpx<R>* __restrict__ out,
+                              int64_t out_stride) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (r >= rows || j >= n_omega) return;
   const cpx<double> v = acc[(int64_t)j * acc_stride + r];
-  out[(int64_t)j * out_stride + r] = mk<R>(R(v.re * scale), R(v.im * scale));
+  const double f = pscale ? scale * pscale[r % n] : scale;
+  out[(int64_t)j * out_stride + r] = mk<R>(R(v.re * f), R(v.im * f));
+}
+
+// out[j][r] = in[j][r] * s[r mod n] (products in FP64, rounded to the element type)
+template <typename R>
+__global__ void scale_block_kernel(const cpx<R>* in, int64_t in_stride, cpx<R>* out, int64_t out_stride,
+                                   int64_t rows, int64_t n, const double* __restrict__ s) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (r >= rows) return;
+  const double f = s[r % n];
+  const cpx<R> v = in[(int64_t)j * in_stride + r];
+  out[(int64_t)j * out_stride + r] = mk<R>(R((double)v.re * f), R((double)v.im * f));
 }
 
 }  // namespace
@@ -230,9 +244,18 @@ cudaError_t launch_analysis(const TileGeom& g, const void* Y, int s0, int s1, co
 
 template <typename R>
 cudaError_t launch_finish(const cpx<double>* acc, int64_t acc_stride, int n_omega, int64_t rows, double scale,
-                          void* out, int64_t out_stride, cudaStream_t st) {
+                          void* out, int64_t out_stride, cudaStream_t st, const double* pscale, int64_t n) {
   dim3 grid((unsigned)((rows + 255) / 256), (unsigned)n_omega);
-  finish_kernel<R><<<grid, 256, 0, st>>>(acc, acc_stride, n_omega, rows, scale, (cpx<R>*)out, out_stride);
+  finish_kernel<R><<<grid, 256, 0, st>>>(acc, acc_stride, n_omega, rows, scale, pscale, n > 0 ? n : rows,
+                                         (cpx<R>*)out, out_stride);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_scale_block(const void* in, int64_t in_stride, void* out, int64_t out_stride, int n_omega,
+                               int64_t rows, int64_t n, const double* s, cudaStream_t st) {
+  dim3 grid((unsigned)((rows + 255) / 256), (unsigned)n_omega);
+  scale_block_kernel<R><<<grid, 256, 0, st>>>((const cpx<R>*)in, in_stride, (cpx<R>*)out, out_stride, rows, n, s);
   return cudaGetLastError();
 }
 
@@ -247,8 +270,12 @@ template cudaError_t launch_analysis<double>(const TileGeom&, const void*, int, 
 template cudaError_t launch_analysis<float>(const TileGeom&, const void*, int, int, const void*, const int64_t*,
                                            bool, cpx<double>*, int64_t, cudaStream_t);
 template cudaError_t launch_finish<double>(const cpx<double>*, int64_t, int, int64_t, double, void*, int64_t,
-                                          cudaStream_t);
+                                          cudaStream_t, const double*, int64_t);
 template cudaError_t launch_finish<float>(const cpx<double>*, int64_t, int, int64_t, double, void*, int64_t,
-                                         cudaStream_t);
+                                         cudaStream_t, const double*, int64_t);
+template cudaError_t launch_scale_block<double>(const void*, int64_t, void*, int64_t, int, int64_t, int64_t,
+                                               const double*, cudaStream_t);
+template cudaError_t launch_scale_block<float>(const void*, int64_t, void*, int64_t, int, int64_t, int64_t,
+                                              const double*, cudaStream_t);
 
 }  // namespace rsv

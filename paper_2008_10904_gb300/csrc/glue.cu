@@ -20,7 +20,6 @@
 
 namespace rsv {
 
-rsv_status march_any(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out, bool adjoint);
 
 namespace {
 
@@ -145,21 +144,110 @@ cudaError_t combine_from_host(rsv_operator op, const void* in, int ka, int kb, c
   return e != cudaSuccess ? e : es;
 }
 
-// CholeskyQR2 of every (frequency, instance) block of X, in place.
+// CholeskyQR2 of every (frequency, instance) block of X, in place.  With r_out (host,
+// [n_omega][n_inst][k][k]) the combined triangular factor X = Q R, R = R2 R1, is returned too.
 template <typename R>
-rsv_status orthonormalize(rsv_operator op, void* X, int k) {
-  std::vector<cd> G, M((size_t)op->n_omega * op->n_inst * k * k), Rf(k * k);
+rsv_status orthonormalize(rsv_operator op, void* X, int k, cd* r_out = nullptr) {
+  const size_t nb = (size_t)op->n_omega * op->n_inst;
+  std::vector<cd> G, M(nb * k * k), Rf(k * k), R1;
+  if (r_out) R1.assign(nb * k * k, cd(0));
   for (int pass = 0; pass < 2; ++pass) {
     cudaError_t e = gram_to_host<R>(op, X, k, G);
     if (e != cudaSuccess) return cuda_fail(e, "gram");
-    for (size_t b = 0; b < (size_t)op->n_omega * op->n_inst; ++b) {
+    for (size_t b = 0; b < nb; ++b) {
       if (!cholesky_upper(&G[b * k * k], k, Rf.data()))
         return fail(RSV_ERR_DIVERGED, "block lost rank in CholeskyQR (frequency " +
                                           std::to_string(b / op->n_inst) + ")");
       invert_upper(Rf.data(), k, &M[b * k * k]);
+      if (r_out && pass == 0) std::copy(Rf.begin(), Rf.end(), R1.begin() + b * k * k);
+      if (r_out && pass == 1) {
+        cd* Rt = r_out + b * k * k;   // R2 R1 (both upper triangular)
+        for (int i = 0; i < k; ++i)
+          for (int j = 0; j < k; ++j) {
+            cd acc = 0;
+            for (int l = i; l <= j; ++l) acc += Rf[i * k + l] * R1[b * k * k + l * k + j];
+            Rt[i * k + j] = acc;
+          }
+      }
     }
     e = combine_from_host<R>(op, X, k, k, M, X, k);
     if (e != cudaSuccess) return cuda_fail(e, "qr combine");
+  }
+  return RSV_OK;
+}
+
+// Modes of the weighted problem back to the forcing / response spaces: x <- x * row (per point).
+template <typename R>
+cudaError_t unweight_modes(rsv_operator op, void* modes, int n_modes, int row) {
+  if (!op->have_weights || modes == nullptr) return cudaSuccess;
+  const int64_t rows = (int64_t)n_modes * op->n;
+  return launch_scale_block<R>(modes, rows, modes, rows, op->n_omega, rows, op->n, op->d_wt + (size_t)row * op->n,
+                               op->stream);
+}
+
+// Imaginary parts of the w = 0 rows of a block of a real-state operator are dropped (the march
+// ignores them as input: the forcing of a real system at w = 0 is real).
+template <typename R>
+cudaError_t zero_rows_imag(rsv_operator op, void* X, int k) {
+  if (!op->real_state) return cudaSuccess;
+  for (int j = 0; j < op->n_omega; ++j) {
+    if (op->pj[j] != 0) continue;
+    char* row = static_cast<char*>(X) + (size_t)j * k * op->n * 2 * sizeof(R) + sizeof(R);
+    cudaError_t e = cudaMemset2DAsync(row, 2 * sizeof(R), 0, sizeof(R), (size_t)k * op->n, op->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Rayleigh-Ritz step on a basis (App. A): Q = qr(basis), Y = R Q, Y^H Y = W S^2 W^H; gains S,
+// forcing modes Q W, response modes Y W S^{-1}.
+template <typename R>
+rsv_status refine_impl(rsv_operator op, const void* basis, int k, int n_modes, const rsv_march_opts* opts,
+                       double* gains, void* fmodes, void* rmodes) {
+  const size_t blk = (size_t)op->n_omega * k * op->n * 2 * sizeof(R);
+  rsv_status s;
+  if ((s = ensure(op->ws_glue_a, blk)) != RSV_OK) return s;
+  if ((s = ensure(op->ws_glue_b, blk)) != RSV_OK) return s;
+  void* Q = op->ws_glue_a.ptr;
+  void* Y = op->ws_glue_b.ptr;
+  cudaError_t e = cudaMemcpyAsync(Q, basis, blk, cudaMemcpyDeviceToDevice, op->stream);
+  if (e == cudaSuccess) e = zero_rows_imag<R>(op, Q, k);
+  // with metrics: W_f-orthonormalising the basis is orthonormalising W_f^{1/2} basis
+  if (e == cudaSuccess && op->have_weights)
+    e = launch_scale_block<R>(Q, (int64_t)k * op->n, Q, (int64_t)k * op->n, op->n_omega, (int64_t)k * op->n, op->n,
+                              op->d_wt + (size_t)8 * op->n, op->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "refinement basis");
+  if ((s = orthonormalize<R>(op, Q, k)) != RSV_OK) return s;
+  if ((s = march_any(op, Q, k, opts, Y, false, SCALE_TILDE)) != RSV_OK) return s;
+  std::vector<cd> G;
+  e = gram_to_host<R>(op, Y, k, G);
+  if (e != cudaSuccess) return cuda_fail(e, "gram");
+  const size_t nb = (size_t)op->n_omega * op->n_inst;
+  std::vector<cd> Mf(nb * k * n_modes), Mr(nb * k * n_modes), V(k * k);
+  std::vector<double> lam(k);
+  for (int j = 0; j < op->n_omega; ++j) {
+    for (int i = 0; i < op->n_inst; ++i) {
+      const size_t b = (size_t)j * op->n_inst + i;
+      jacobi_eig(&G[b * k * k], k, lam.data(), V.data());
+      for (int m = 0; m < n_modes; ++m) {
+        const double sg = std::sqrt(std::max(lam[m], 0.0));
+        gains[((size_t)i * op->n_omega + j) * n_modes + m] = sg;
+        for (int a = 0; a < k; ++a) {
+          Mf[(b * k + a) * n_modes + m] = V[a * k + m];
+          Mr[(b * k + a) * n_modes + m] = sg > 0 ? V[a * k + m] / sg : cd(0);
+        }
+      }
+    }
+  }
+  if (fmodes) {
+    e = combine_from_host<R>(op, Q, k, n_modes, Mf, fmodes, n_modes);
+    if (e == cudaSuccess) e = unweight_modes<R>(op, fmodes, n_modes, 6);
+    if (e != cudaSuccess) return cuda_fail(e, "forcing modes");
+  }
+  if (rmodes) {
+    e = combine_from_host<R>(op, Y, k, n_modes, Mr, rmodes, n_modes);
+    if (e == cudaSuccess) e = unweight_modes<R>(op, rmodes, n_modes, 7);
+    if (e != cudaSuccess) return cuda_fail(e, "response modes");
   }
   return RSV_OK;
 }
@@ -173,15 +261,15 @@ rsv_status gains_impl(rsv_operator op, const void* omega_block, int k, int q, in
   if ((s = ensure(op->ws_glue_b, blk)) != RSV_OK) return s;
   void* A = op->ws_glue_a.ptr;
   void* B = op->ws_glue_b.ptr;
-  if ((s = march_any(op, omega_block, k, opts, A, false)) != RSV_OK) return s;
+  if ((s = march_any(op, omega_block, k, opts, A, false, SCALE_TILDE)) != RSV_OK) return s;
   for (int it = 0; it < q; ++it) {
     if ((s = orthonormalize<R>(op, A, k)) != RSV_OK) return s;
-    if ((s = march_any(op, A, k, opts, B, true)) != RSV_OK) return s;
+    if ((s = march_any(op, A, k, opts, B, true, SCALE_TILDE)) != RSV_OK) return s;
     if ((s = orthonormalize<R>(op, B, k)) != RSV_OK) return s;
-    if ((s = march_any(op, B, k, opts, A, false)) != RSV_OK) return s;
+    if ((s = march_any(op, B, k, opts, A, false, SCALE_TILDE)) != RSV_OK) return s;
   }
   if ((s = orthonormalize<R>(op, A, k)) != RSV_OK) return s;
-  if ((s = march_any(op, A, k, opts, B, true)) != RSV_OK) return s;
+  if ((s = march_any(op, A, k, opts, B, true, SCALE_TILDE)) != RSV_OK) return s;
   std::vector<cd> G;
   cudaError_t e = gram_to_host<R>(op, B, k, G);
   if (e != cudaSuccess) return cuda_fail(e, "gram");
@@ -204,11 +292,114 @@ rsv_status gains_impl(rsv_operator op, const void* omega_block, int k, int q, in
   }
   if (rmodes) {
     e = combine_from_host<R>(op, A, k, n_modes, Mu, rmodes, n_modes);
+    if (e == cudaSuccess) e = unweight_modes<R>(op, rmodes, n_modes, 7);
     if (e != cudaSuccess) return cuda_fail(e, "response modes");
   }
   if (fmodes) {
     e = combine_from_host<R>(op, B, k, n_modes, Mv, fmodes, n_modes);
+    if (e == cudaSuccess) e = unweight_modes<R>(op, fmodes, n_modes, 6);
     if (e != cudaSuccess) return cuda_fail(e, "forcing modes");
+  }
+  return RSV_OK;
+}
+
+// Arnoldi (App. A, Eq. (freqOrt)) per frequency and instance, one vector each: f_0 normalised;
+// for it = 0 .. m - 1: y_it = R f_it, w_it = R^H y_it; column it of H holds <f_i, w_it> (i <= it,
+// classical Gram-Schmidt done twice) and the norm beta of the remainder (H[it+1][it]);
+// f_{it+1} = remainder / beta.  Then H psi = gamma^2 psi: gains gamma, forcing modes F psi,
+// response modes Y psi / gamma (F is orthonormal, so R_F = I).
+template <typename R>
+rsv_status arnoldi_impl(rsv_operator op, const void* f0, int m, int n_modes, const rsv_march_opts* opts,
+                        double* gains, void* fmodes, void* rmodes) {
+  const int64_t n = op->n;
+  const int nw = op->n_omega, ni = op->n_inst;
+  const size_t nb = (size_t)nw * ni;
+  const size_t vec = (size_t)nw * n * 2 * sizeof(R);          // one vector per frequency, [n_omega][1][n]
+  rsv_status s;
+  if ((s = ensure(op->ws_glue_a, 2 * (size_t)m * vec)) != RSV_OK) return s;
+  if ((s = ensure(op->ws_glue_b, (size_t)(m + 1) * vec + 3 * vec)) != RSV_OK) return s;
+  char* Fb = static_cast<char*>(op->ws_glue_a.ptr);             // [n_omega][m][n]
+  char* Yb = Fb + (size_t)m * vec;                              // [n_omega][m][n]
+  char* X = static_cast<char*>(op->ws_glue_b.ptr);              // [n_omega][it + 2][n], compact
+  char* cur = X + (size_t)(m + 1) * vec;
+  char* yt = cur + vec;
+  char* wt = yt + vec;
+  const size_t el = 2 * sizeof(R), row = (size_t)n * el;
+  const cudaStream_t st = op->stream;
+  // columns [rows of H][it] per (frequency, instance)
+  std::vector<cd> H(nb * m * m, cd(0)), rfac(nb);
+  cudaError_t e = cudaMemcpyAsync(cur, f0, vec, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = zero_rows_imag<R>(op, cur, 1);
+  if (e != cudaSuccess) return cuda_fail(e, "arnoldi start");
+  if ((s = orthonormalize<R>(op, cur, 1)) != RSV_OK) return s;
+  std::vector<cd> G, M;
+  for (int it = 0; it < m; ++it) {
+    // f_it into the basis (column it of every frequency's block)
+    e = cudaMemcpy2DAsync(Fb + it * row, (size_t)m * row, cur, row, row, nw, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "arnoldi basis");
+    if ((s = march_any(op, cur, 1, opts, yt, false, SCALE_TILDE)) != RSV_OK) return s;
+    if ((s = march_any(op, yt, 1, opts, wt, true, SCALE_TILDE)) != RSV_OK) return s;
+    e = cudaMemcpy2DAsync(Yb + it * row, (size_t)m * row, yt, row, row, nw, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "arnoldi responses");
+    const int kk = it + 2;                                      // f_0 .. f_it and the vector being reduced
+    const char* src = wt;
+    for (int pass = 0; pass < 2; ++pass) {
+      e = cudaMemcpy2DAsync(X, (size_t)kk * row, Fb, (size_t)m * row, (size_t)(it + 1) * row, nw,
+                            cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(X + (size_t)(it + 1) * row, (size_t)kk * row, src, row, row, nw, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = gram_to_host<R>(op, X, kk, G);
+      if (e != cudaSuccess) return cuda_fail(e, "arnoldi projection");
+      M.assign(nb * kk, cd(0));
+      for (size_t b = 0; b < nb; ++b) {
+        for (int i = 0; i <= it; ++i) {
+          const cd th = G[(b * kk + i) * kk + it + 1];            // <f_i, w>
+          H[(b * m + i) * m + it] += th;
+          M[b * kk + i] = -th;
+        }
+        M[b * kk + it + 1] = 1.0;
+      }
+      e = combine_from_host<R>(op, X, kk, 1, M, cur, 1);       // w - F theta
+      if (e != cudaSuccess) return cuda_fail(e, "arnoldi orthogonalisation");
+      src = cur;
+    }
+    if (it + 1 < m) {
+      std::vector<cd> rr(nb);
+      if ((s = orthonormalize<R>(op, cur, 1, rr.data())) != RSV_OK)
+        return fail(RSV_ERR_DIVERGED, "Arnoldi: the Krylov space stopped growing (a frequency's remainder vanished)");
+      for (size_t b = 0; b < nb; ++b) H[(b * m + it + 1) * m + it] = rr[b];
+    }
+  }
+  // eigen-decomposition of the Hermitian part of H per (frequency, instance)
+  std::vector<cd> Mf(nb * m * n_modes), Mr(nb * m * n_modes), Hs(m * m), V(m * m);
+  std::vector<double> lam(m);
+  for (int j = 0; j < nw; ++j) {
+    for (int i = 0; i < ni; ++i) {
+      const size_t b = (size_t)j * ni + i;
+      for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) Hs[r * m + c] = 0.5 * (H[(b * m + r) * m + c] + std::conj(H[(b * m + c) * m + r]));
+      if (op->real_state && op->pj[j] == 0)
+        for (auto& x : Hs) x = x.real();
+      jacobi_eig(Hs.data(), m, lam.data(), V.data());
+      for (int q = 0; q < n_modes; ++q) {
+        const double g = std::sqrt(std::max(lam[q], 0.0));
+        gains[((size_t)i * nw + j) * n_modes + q] = g;
+        for (int a = 0; a < m; ++a) {
+          Mf[(b * m + a) * n_modes + q] = V[a * m + q];
+          Mr[(b * m + a) * n_modes + q] = g > 0 ? V[a * m + q] / g : cd(0);
+        }
+      }
+    }
+  }
+  if (fmodes) {
+    e = combine_from_host<R>(op, Fb, m, n_modes, Mf, fmodes, n_modes);
+    if (e == cudaSuccess) e = unweight_modes<R>(op, fmodes, n_modes, 6);
+    if (e != cudaSuccess) return cuda_fail(e, "forcing modes");
+  }
+  if (rmodes) {
+    e = combine_from_host<R>(op, Yb, m, n_modes, Mr, rmodes, n_modes);
+    if (e == cudaSuccess) e = unweight_modes<R>(op, rmodes, n_modes, 7);
+    if (e != cudaSuccess) return cuda_fail(e, "response modes");
   }
   return RSV_OK;
 }
@@ -217,6 +408,46 @@ rsv_status gains_impl(rsv_operator op, const void* omega_block, int k, int q, in
 }  // namespace rsv
 
 using namespace rsv;
+
+extern "C" rsv_status rsv_arnoldi_gains(rsv_operator op, const void* f0, int32_t m, int32_t n_modes,
+                                        const rsv_march_opts* opts, double* gains, void* fmodes, void* rmodes) {
+  if (!op || !f0 || !gains) return fail(RSV_ERR_INVALID_ARG, "null argument");
+  if (!op->have_freq) return fail(RSV_ERR_STATE, "rsv_set_frequencies must come first");
+  if (m < 1 || m > 31) return fail(RSV_ERR_INVALID_ARG, "m must be 1..31");
+  if (n_modes < 1 || n_modes > m) return fail(RSV_ERR_INVALID_ARG, "n_modes must be 1..m");
+  for (int i = 0; i < op->n_inst; ++i)
+    if (op->inst_len[i] < m) return fail(RSV_ERR_INVALID_ARG, "m exceeds an instance's length");
+  return op->prec == RSV_PREC_FP64 ? arnoldi_impl<double>(op, f0, m, n_modes, opts, gains, fmodes, rmodes)
+                                   : arnoldi_impl<float>(op, f0, m, n_modes, opts, gains, fmodes, rmodes);
+}
+
+namespace {
+rsv_status check_block_args(rsv_operator op, int k) {
+  if (!op->have_freq) return fail(RSV_ERR_STATE, "rsv_set_frequencies must come first");
+  if (k < 1 || k > 32) return fail(RSV_ERR_INVALID_ARG, "k must be 1..32");
+  for (int i = 0; i < op->n_inst; ++i)
+    if (op->inst_len[i] < k) return fail(RSV_ERR_INVALID_ARG, "k exceeds an instance's length");
+  return RSV_OK;
+}
+}  // namespace
+
+extern "C" rsv_status rsv_refine_gains(rsv_operator op, const void* basis, int32_t k, int32_t n_modes,
+                                       const rsv_march_opts* opts, double* gains, void* fmodes, void* rmodes) {
+  if (!op || !basis || !gains) return fail(RSV_ERR_INVALID_ARG, "null argument");
+  rsv_status s = check_block_args(op, k);
+  if (s != RSV_OK) return s;
+  if (n_modes < 1 || n_modes > k) return fail(RSV_ERR_INVALID_ARG, "n_modes must be 1..k");
+  return op->prec == RSV_PREC_FP64 ? refine_impl<double>(op, basis, k, n_modes, opts, gains, fmodes, rmodes)
+                                   : refine_impl<float>(op, basis, k, n_modes, opts, gains, fmodes, rmodes);
+}
+
+extern "C" rsv_status rsv_orthonormalize(rsv_operator op, void* block, int32_t k, double* r_factor) {
+  if (!op || !block) return fail(RSV_ERR_INVALID_ARG, "null argument");
+  rsv_status s = check_block_args(op, k);
+  if (s != RSV_OK) return s;
+  cd* r = reinterpret_cast<cd*>(r_factor);
+  return op->prec == RSV_PREC_FP64 ? orthonormalize<double>(op, block, k, r) : orthonormalize<float>(op, block, k, r);
+}
 
 extern "C" rsv_status rsv_gains_modes(rsv_operator op, const void* omega_block, int32_t k, int32_t n_power_iter,
                                       int32_t n_modes, const rsv_march_opts* opts, double* gains, void* fmodes,

@@ -1,13 +1,14 @@
 // Direct march that allocates nothing: rsv_march_direct_static.
 //
 // Some callers cannot call cudaMalloc once they are running: a solver that
-// hands this library a fixed device-memory budget at start-up and forbids
-// later growth, a host thread that records work into a CUDA stream capture
-// where a synchronous allocation would break the capture, or a real-time
-// loop that must never wait on the allocator.  rsv_march_direct grows its
-// workspace lazily and therefore may allocate on any call.  This variant
-// keeps all of the march's scratch (state, forcing tile, snapshot tile, FP64
-// accumulators) in one file-scope device array of fixed size instead.
+// reserves the device memory for its own pool at start-up and forbids any
+// later allocation, or a real-time loop that must never stall on the
+// allocator (cudaMalloc / cudaFree may synchronise the whole device).
+// rsv_march_direct grows its workspace lazily and therefore may allocate on
+// any call.  This variant keeps all of the march's scratch (state, forcing
+// tile, snapshot tile, FP64 accumulators) in one file-scope device array of
+// fixed size instead.  The call still ends by synchronising the operator's
+// stream, as every entry point of the library does.
 //
 // The array exists once per GPU that loads the library and stays allocated
 // until the process exits.  Every call shares it and it keeps the contents
@@ -174,6 +175,9 @@ extern "C" rsv_status rsv_march_direct_static(rsv_operator op, const void* f_hat
   if (op->kind != RSV_OP_GL1D)
     return fail(RSV_ERR_INVALID_ARG, "rsv_march_direct_static supports the three-point (GL1D) operator kind only");
   if (f_hat == y_hat) return fail(RSV_ERR_INVALID_ARG, "input and output blocks must not alias");
+  if (op->have_weights)
+    return fail(RSV_ERR_INVALID_ARG, "rsv_march_direct_static applies no forcing / observation weights: clear them "
+                                     "with rsv_set_weights(op, NULL, NULL, NULL, NULL)");
   return op->prec == RSV_PREC_FP64 ? march_static_impl<double>(op, f_hat, k, opts, y_hat)
                                    : march_static_impl<float>(op, f_hat, k, opts, y_hat);
 }

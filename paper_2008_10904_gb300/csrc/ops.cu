@@ -171,7 +171,76 @@ __global__ void vec_sumsq_kernel(const T* __restrict__ x, int64_t vals_per_vec, 
     atomicAdd(out + blockIdx.y, t);
   }
 }
+// out[i] += sum of squares of the values of instance i of one vector (FP64 sums; out zeroed by the caller).
+template <typename T>
+__global__ void inst_sumsq_kernel(const T* __restrict__ x, const int64_t* __restrict__ inst_off, int vals_per_point,
+                                  double* __restrict__ out) {
+  const int inst = blockIdx.y;
+  const int64_t a = inst_off[inst] * vals_per_point, b = inst_off[inst + 1] * vals_per_point;
+  double acc = 0.0;
+  for (int64_t e = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < b; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)x[e];
+    acc += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    atomicAdd(out + inst, t);
+  }
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): value i of stream `seed`.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// x[e] = 2 (z_e >> 11) 2^-53 - 1 for the interleaved values e of the state (exact in FP64).
+template <typename T>
+__global__ void probe_init_kernel(T* __restrict__ x, int64_t vals, uint64_t seed) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < vals; e += (int64_t)gridDim.x * blockDim.x) {
+    const double u = 2.0 * (double)(splitmix64_at(seed, (uint64_t)e) >> 11) * 0x1.0p-53 - 1.0;
+    x[e] = (T)u;
+  }
+}
 }  // namespace
+
+// Per-instance squared 2-norms of vector 0 of the march state after step n_end (kg = 1 layout).
+cudaError_t instance_sq_norms(rsv_operator op, int64_t n_end, double* d_out) {
+  const size_t elem = op->prec == RSV_PREC_FP64 ? 8 : 4;
+  const int vpp = op->real_state ? 1 : 2;
+  const char* st = static_cast<const char*>(op->ws_state.ptr);
+  if (op->kind == RSV_OP_DENSE) st += (size_t)(n_end & 1) * (size_t)op->n * vpp * elem;
+  cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * op->n_inst, op->stream);
+  if (e != cudaSuccess) return e;
+  int64_t max_len = 1;
+  for (int i = 0; i < op->n_inst; ++i) max_len = std::max(max_len, op->inst_len[i]);
+  const unsigned bx = (unsigned)std::min<int64_t>((max_len * vpp + 255) / 256, 2 * std::max(op->sm_count, 1));
+  dim3 grid(std::max(bx, 1u), (unsigned)op->n_inst);
+  const int64_t* off = (const int64_t*)op->d_inst_off;
+  if (op->prec == RSV_PREC_FP64)
+    inst_sumsq_kernel<double><<<grid, 256, 0, op->stream>>>((const double*)st, off, vpp, d_out);
+  else
+    inst_sumsq_kernel<float><<<grid, 256, 0, op->stream>>>((const float*)st, off, vpp, d_out);
+  return cudaGetLastError();
+}
+
+// The decay probe's random initial state in vector 0 of the march state (step 0 layout).
+cudaError_t probe_initial_state(rsv_operator op, uint64_t seed) {
+  const int64_t vals = (op->real_state ? 1 : 2) * op->n;
+  const unsigned blocks = (unsigned)std::min<int64_t>((vals + 255) / 256, 8 * std::max(op->sm_count, 1));
+  if (op->prec == RSV_PREC_FP64)
+    probe_init_kernel<double><<<blocks, 256, 0, op->stream>>>((double*)op->ws_state.ptr, vals, seed);
+  else
+    probe_init_kernel<float><<<blocks, 256, 0, op->stream>>>((float*)op->ws_state.ptr, vals, seed);
+  return cudaGetLastError();
+}
 
 // Squared 2-norm of each of the kg vectors of the march state after step n_end
 // (the dense path keeps two step-parity copies of the state).

@@ -123,6 +123,8 @@ rsv_operator_s::~rsv_operator_s() {
   if (d_pj) cudaFree(d_pj);
   if (d_cw) cudaFree(d_cw);
   if (d_flag) cudaFree(d_flag);
+  if (d_wt) cudaFree(d_wt);
+  if (ws_scaled.ptr) cudaFree(ws_scaled.ptr);
   for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
 }
 
@@ -351,6 +353,7 @@ extern "C" rsv_status rsv_set_frequencies(rsv_operator op, const double* omega, 
   op->n_t = n_t;
   op->h = period / (double)n_t;
   op->have_freq = true;
+  op->probe_memo.clear();
   rsv_status ks = on_frequencies(op);
   if (ks != RSV_OK) {
     op->have_freq = false;
@@ -363,17 +366,113 @@ extern "C" rsv_status rsv_set_frequencies(rsv_operator op, const double* omega, 
 
 namespace rsv {
 
+// Decay run (Sec. 2.3): unforced march of one random state in tiles of `every` steps; per-instance
+// norm ratios at the tile ends.  Returns OK with the steps at the first check point where every
+// ratio is <= tol, UNSTABLE when a ratio passes 1e6 / turns non-finite or max_steps pass first.
+template <typename R>
+static rsv_status probe_impl(rsv_operator op, bool adjoint, double tol, int64_t max_steps, uint64_t seed, int every,
+                             int64_t* steps_out, double* ratio_out) {
+  const size_t se = state_elem_bytes(op);
+  const int ni = op->n_inst;
+  rsv_status st;
+  if ((st = ensure(op->ws_state, (size_t)op->n * se + stage_scratch_bytes(op, 1))) != RSV_OK) return st;
+  if ((st = ensure(op->ws_norm, (size_t)2 * ni * sizeof(double))) != RSV_OK) return st;
+  double* d_tile_norms = (double*)op->ws_norm.ptr;   // written by the 1-D tile kernel
+  double* d_inst = d_tile_norms + ni;
+  const cudaStream_t stream = op->stream;
+  cudaError_t e = cudaMemsetAsync(op->ws_state.ptr, 0, (size_t)op->n * se + stage_scratch_bytes(op, 1), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(op->d_flag, 0, sizeof(int), stream);
+  if (e == cudaSuccess) e = probe_initial_state(op, seed);
+  std::vector<double> n0(ni), nn(ni);
+  if (e == cudaSuccess) e = instance_sq_norms(op, 0, d_inst);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(n0.data(), d_inst, sizeof(double) * ni, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "decay probe set-up");
+  int64_t done = 0;
+  double ratio = 1.0;
+  while (done < max_steps) {
+    MarchTile mt;
+    mt.n0 = done;
+    mt.steps = (int)std::min<int64_t>(every, max_steps - done);
+    mt.n_forced = 0;
+    mt.y_first = mt.steps;
+    mt.kg = 1;
+    mt.adjoint = adjoint;
+    {
+      ProfScope ps(op, PROF_MARCH, march_tile_kernels(op, mt.steps, 1));
+      e = march_tile<R>(op, mt, op->ws_state.ptr, nullptr, nullptr, d_tile_norms);
+    }
+    done += mt.steps;
+    int flag = 0;
+    if (e == cudaSuccess) e = instance_sq_norms(op, done, d_inst);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nn.data(), d_inst, sizeof(double) * ni, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, op->d_flag, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "decay probe");
+    ratio = 0.0;
+    bool finite = flag == 0;
+    for (int i = 0; i < ni; ++i) {
+      const double r = std::sqrt(nn[i] / n0[i]);
+      if (!std::isfinite(r)) finite = false;
+      ratio = std::max(ratio, r);
+    }
+    if (steps_out) *steps_out = done;
+    if (ratio_out) *ratio_out = finite ? ratio : INFINITY;
+    if (!finite || ratio > 1e6)
+      return fail(RSV_ERR_UNSTABLE, "decay probe: the state norm grew (ratio " + std::to_string(ratio) + " after " +
+                                        std::to_string(done) + " steps): the system is not stable");
+    if (ratio <= tol) return RSV_OK;
+  }
+  return fail(RSV_ERR_UNSTABLE, "decay probe: the state norm did not fall to tol within " +
+                                    std::to_string(max_steps) + " steps (ratio " + std::to_string(ratio) + ")");
+}
+
+static rsv_status probe_any(rsv_operator op, bool adjoint, double tol, int64_t max_steps, uint64_t seed, int every,
+                            int64_t* steps, double* ratio) {
+  if (!(tol > 0.0 && tol < 1.0)) return fail(RSV_ERR_INVALID_ARG, "decay tol must be in (0, 1)");
+  if (max_steps < 1) return fail(RSV_ERR_INVALID_ARG, "decay max_steps must be >= 1");
+  if (every <= 0) every = default_tile_steps(op);
+  return op->prec == RSV_PREC_FP64 ? probe_impl<double>(op, adjoint, tol, max_steps, seed, every, steps, ratio)
+                                   : probe_impl<float>(op, adjoint, tol, max_steps, seed, every, steps, ratio);
+}
+
 struct Schedule {
   int64_t total, first, forced;
 };
 
-static rsv_status make_schedule(rsv_operator op, const rsv_march_opts* o, Schedule* s) {
+// Transient windows for n_transient_windows = -1: the decay run's length in windows, remembered per
+// direction and setting until the frequencies change.
+static rsv_status auto_windows(rsv_operator op, const rsv_march_opts* o, bool adjoint, int64_t* windows) {
+  const double tol = o->decay_tol > 0.0 ? o->decay_tol : 1e-8;
+  const int64_t cap = o->decay_max_steps > 0 ? o->decay_max_steps : 1000 * op->n_t;
+  const int every = o->tile_steps > 0 ? o->tile_steps : default_tile_steps(op);
+  for (const auto& m : op->probe_memo) {
+    if (m.adjoint == (int)adjoint && m.tol == tol && m.max_steps == cap && m.seed == o->decay_seed && m.every == every) {
+      *windows = (m.steps + op->n_t - 1) / op->n_t;
+      return RSV_OK;
+    }
+  }
+  int64_t steps = 0;
+  rsv_status st = probe_any(op, adjoint, tol, cap, o->decay_seed, every, &steps, nullptr);
+  if (st != RSV_OK) return st;
+  op->probe_memo.push_back({(int)adjoint, tol, cap, o->decay_seed, every, steps});
+  *windows = (steps + op->n_t - 1) / op->n_t;
+  return RSV_OK;
+}
+
+static rsv_status make_schedule(rsv_operator op, const rsv_march_opts* o, bool adjoint, Schedule* s) {
   rsv_march_opts def{};
   if (!o) o = &def;
   if (o->variant == RSV_SSRM) {
-    if (o->n_transient_windows < 0) return fail(RSV_ERR_INVALID_ARG, "n_transient_windows < 0");
-    s->total = (int64_t)(o->n_transient_windows + 1) * op->n_t;
-    s->first = (int64_t)o->n_transient_windows * op->n_t;
+    int64_t nw = o->n_transient_windows;
+    if (nw == -1) {
+      rsv_status st = auto_windows(op, o, adjoint, &nw);
+      if (st != RSV_OK) return st;
+    } else if (nw < 0) {
+      return fail(RSV_ERR_INVALID_ARG, "n_transient_windows must be >= 0, or -1 for the decay probe");
+    }
+    s->total = (nw + 1) * op->n_t;
+    s->first = nw * op->n_t;
     s->forced = s->total;
   } else if (o->variant == RSV_TRM) {
     if (o->tail_steps < 0) return fail(RSV_ERR_INVALID_ARG, "tail_steps < 0");
@@ -387,11 +486,33 @@ static rsv_status make_schedule(rsv_operator op, const rsv_march_opts* o, Schedu
   return RSV_OK;
 }
 
+// Per-point factors of the weighted runs (rsv_set_weights), rows of op->d_wt.
+enum { WT_B = 0, WT_C, WT_CWY, WT_B_WF, WT_B_SWF, WT_C_SWY, WT_ISWF, WT_ISWY, WT_SWF };
+
+// Input and output scalings of one march: SCALE_PLAIN gives yhat = C R B fhat (direct) and
+// what = W_f^{-1} B^H R^H C^H W_y yhat (adjoint); SCALE_TILDE gives the runs of
+// W_y^{1/2} C R B W_f^{-1/2} and its conjugate transpose (the randomized SVD's operator).
+static void march_scalings(rsv_operator op, int scaling, bool adjoint, const double** sin, const double** sout) {
+  *sin = *sout = nullptr;
+  if (!op->have_weights || scaling == SCALE_NONE) return;
+  const int64_t n = op->n;
+  auto row = [&](int r) { return op->d_wt + (size_t)r * n; };
+  if (scaling == SCALE_PLAIN) {
+    *sin = adjoint ? row(WT_CWY) : row(WT_B);
+    *sout = adjoint ? row(WT_B_WF) : row(WT_C);
+  } else {
+    *sin = adjoint ? row(WT_C_SWY) : row(WT_B_SWF);
+    *sout = adjoint ? row(WT_B_SWF) : row(WT_C_SWY);
+  }
+}
+
 template <typename R>
 static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out,
-                             bool adjoint) {
+                             bool adjoint, int scaling) {
+  const double *s_in = nullptr, *s_out = nullptr;
+  march_scalings(op, scaling, adjoint, &s_in, &s_out);
   Schedule sc;
-  rsv_status st = make_schedule(op, opts, &sc);
+  rsv_status st = make_schedule(op, opts, adjoint, &sc);
   if (st != RSV_OK) return st;
   const int64_t n = op->n;
   const size_t se = state_elem_bytes(op);
@@ -413,6 +534,7 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
       const double rows_ = (double)kg_ * n;
       double b = rows_ * se + (double)stage_scratch_bytes(op, kg_) + (2.0 * s_ + 1) * rows_ * se + s_ * rows_ * se;
       if (op->prec != RSV_PREC_FP64) b += (double)op->n_omega * rows_ * sizeof(cpx<double>);
+      if (s_in) b += (double)op->n_omega * rows_ * coef_bytes(op);
       if (op->kind == RSV_OP_DENSE) b += 2.0 * op->n_omega * rows_ * 2 * sizeof(R);
       return b;
     };
@@ -464,10 +586,19 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
     g.m4 = 4 * op->n_t;
     const void* fh = nullptr;
     int synth_stride = 1;
+    const void* gin = static_cast<const char*>(in) + (size_t)v0 * n * ce;
+    int64_t gin_stride = (int64_t)k * n;
+    if (s_in) {   // the group's coefficients times the input scaling (B, or C W_y for the adjoint)
+      if ((st = ensure(op->ws_scaled, (size_t)op->n_omega * rows * ce)) != RSV_OK) return st;
+      ProfScope ps(op, PROF_GLUE);
+      e = launch_scale_block<R>(gin, gin_stride, op->ws_scaled.ptr, rows, op->n_omega, rows, n, s_in, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "input scaling");
+      gin = op->ws_scaled.ptr;
+      gin_stride = rows;
+    }
     {
       ProfScope ps(op, PROF_GLUE, op->kind == RSV_OP_DENSE ? (kv == k ? 3 : 2 * op->n_omega + 1) : 0);
-      st = prepare_coefficients<R>(op, static_cast<const char*>(in) + (size_t)v0 * n * ce, (int64_t)k * n, kv, adjoint,
-                                   &fh, &g.coef_stride, &synth_stride);
+      st = prepare_coefficients<R>(op, gin, gin_stride, kv, adjoint, &fh, &g.coef_stride, &synth_stride);
     }
     if (st != RSV_OK) return st;
     g.tau_stride = synth_stride;
@@ -536,7 +667,8 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
     }
     if (!truncate) op->last_steps = sc.total;
     void* o = static_cast<char*>(out) + (size_t)v0 * n * ce;
-    e = launch_finish<R>(acc, acc_stride, op->n_omega, rows, 1.0 / (double)op->n_t, o, (int64_t)k * n, stream);
+    e = launch_finish<R>(acc, acc_stride, op->n_omega, rows, 1.0 / (double)op->n_t, o, (int64_t)k * n, stream,
+                         s_out, n);
     if (e != cudaSuccess) return cuda_fail(e, "finish");
   }
   int flag = 0;
@@ -548,24 +680,63 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
   return RSV_OK;
 }
 
-rsv_status march_any(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out, bool adjoint) {
+rsv_status march_any(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out, bool adjoint,
+                     int scaling) {
   if (!op || !in || !out || k < 1) return fail(RSV_ERR_INVALID_ARG, "bad march arguments");
   if (!op->have_freq) return fail(RSV_ERR_STATE, "rsv_set_frequencies must come first");
   if (in == out) return fail(RSV_ERR_INVALID_ARG, "input and output blocks must not alias");
-  return op->prec == RSV_PREC_FP64 ? march_impl<double>(op, in, k, opts, out, adjoint)
-                                   : march_impl<float>(op, in, k, opts, out, adjoint);
+  return op->prec == RSV_PREC_FP64 ? march_impl<double>(op, in, k, opts, out, adjoint, scaling)
+                                   : march_impl<float>(op, in, k, opts, out, adjoint, scaling);
 }
 
 }  // namespace rsv
 
 extern "C" rsv_status rsv_march_direct(rsv_operator op, const void* f_hat, int32_t k, const rsv_march_opts* opts,
                                        void* y_hat) {
-  return march_any(op, f_hat, k, opts, y_hat, false);
+  return march_any(op, f_hat, k, opts, y_hat, false, SCALE_PLAIN);
 }
 
 extern "C" rsv_status rsv_march_adjoint(rsv_operator op, const void* y_hat, int32_t k, const rsv_march_opts* opts,
                                         void* w_hat) {
-  return march_any(op, y_hat, k, opts, w_hat, true);
+  return march_any(op, y_hat, k, opts, w_hat, true, SCALE_PLAIN);
+}
+
+// Diagonal B, C, W_f, W_y (Sec. 2.1).  The per-point factors the runs use are formed here in FP64.
+extern "C" rsv_status rsv_set_weights(rsv_operator op, const double* b, const double* c, const double* w_f,
+                                      const double* w_y) {
+  if (!op) return fail(RSV_ERR_INVALID_ARG, "null operator");
+  if (op->d_wt) cudaFree(op->d_wt);
+  op->d_wt = nullptr;
+  op->have_weights = false;
+  if (!b && !c && !w_f && !w_y) return RSV_OK;
+  const int64_t n = op->n;
+  std::vector<double> t((size_t)9 * n);
+  for (int64_t p = 0; p < n; ++p) {
+    const double bp = b ? b[p] : 1.0, cp = c ? c[p] : 1.0, wf = w_f ? w_f[p] : 1.0, wy = w_y ? w_y[p] : 1.0;
+    if (!(bp >= 0.0 && std::isfinite(bp)) || !(cp >= 0.0 && std::isfinite(cp)))
+      return fail(RSV_ERR_INVALID_ARG, "forcing and observation entries must be finite and >= 0");
+    if (!(wf > 0.0 && std::isfinite(wf)) || !(wy > 0.0 && std::isfinite(wy)))
+      return fail(RSV_ERR_INVALID_ARG, "metric entries must be finite and > 0");
+    const double v[9] = {bp, cp, cp * wy, bp / wf, bp / std::sqrt(wf), cp * std::sqrt(wy), 1.0 / std::sqrt(wf),
+                         1.0 / std::sqrt(wy), std::sqrt(wf)};
+    for (int r = 0; r < 9; ++r) t[(size_t)r * n + p] = v[r];
+  }
+  cudaError_t e = cudaMalloc(&op->d_wt, t.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(op->d_wt, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (op->d_wt) cudaFree(op->d_wt);
+    op->d_wt = nullptr;
+    return cuda_fail(e, "weights upload");
+  }
+  op->have_weights = true;
+  return RSV_OK;
+}
+
+extern "C" rsv_status rsv_decay_probe(rsv_operator op, int32_t adjoint, double tol, int64_t max_steps, uint64_t seed,
+                                      int32_t check_every, int64_t* steps, double* ratio) {
+  if (!op) return fail(RSV_ERR_INVALID_ARG, "null operator");
+  if (!op->have_freq) return fail(RSV_ERR_STATE, "rsv_set_frequencies must come first (it sets the step)");
+  return probe_any(op, adjoint != 0, tol, max_steps, seed, check_every, steps, ratio);
 }
 
 extern "C" rsv_status rsv_apply_operator(rsv_operator op, const void* x, int32_t k, int32_t adjoint, void* y) {

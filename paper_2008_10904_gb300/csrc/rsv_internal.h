@@ -145,6 +145,21 @@ struct rsv_operator_s {
   bool tc_contract_disabled = false;   // keep the synthesis / analysis on the CUDA cores
   int* d_flag = nullptr;
   rsv::Profiler prof;
+  // diagonal forcing / observation matrices and metrics (rsv_set_weights): per-point FP64 factors
+  // [b, c, c w_y, b / w_f, b / sqrt(w_f), c sqrt(w_y), 1 / sqrt(w_f), 1 / sqrt(w_y), sqrt(w_f)]
+  bool have_weights = false;
+  double* d_wt = nullptr;               // [9][n]
+  rsv::Workspace ws_scaled;             // scaled input coefficients of one vector group
+  // decay-probe results (n_transient_windows = -1), valid for the current frequency grid
+  struct ProbeMemo {
+    int adjoint;
+    double tol;
+    int64_t max_steps;
+    uint64_t seed;
+    int every;
+    int64_t steps;
+  };
+  std::vector<ProbeMemo> probe_memo;
   int last_tile = 0, last_group = 0;   // tile length and vector-group size of the latest march
   int64_t last_steps = 0;              // steps marched by the latest march's last vector group
 
@@ -166,6 +181,11 @@ struct ProfScope {
   ~ProfScope();
 };
 enum { PROF_SYNTH = 0, PROF_MARCH = 1, PROF_ANALYSIS = 2, PROF_GLUE = 3 };
+// scalings of a march by the weights of rsv_set_weights: none, the plain runs of R_y and R_y^dag,
+// or the runs of W_y^{1/2} C R B W_f^{-1/2} and its conjugate transpose
+enum { SCALE_NONE = 0, SCALE_PLAIN = 1, SCALE_TILDE = 2 };
+rsv_status march_any(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out, bool adjoint,
+                     int scaling);
 
 // ----- launchers (contract_kernels.cu) -------------------------------------
 struct TileGeom {
@@ -189,10 +209,15 @@ template <typename R>
 cudaError_t launch_analysis(const TileGeom& g, const void* Y, int s0, int s1, const void* tw,
                             const int64_t* pj, bool real_state, cpx<double>* acc, int64_t acc_stride,
                             cudaStream_t st);
-// out[j][r] = acc[j][r] * scale (converted to the element type R)
+// out[j][r] = acc[j][r] * scale (* pscale[r mod n] when given), converted to the element type R
 template <typename R>
 cudaError_t launch_finish(const cpx<double>* acc, int64_t acc_stride, int n_omega, int64_t rows,
-                          double scale, void* out, int64_t out_stride, cudaStream_t st);
+                          double scale, void* out, int64_t out_stride, cudaStream_t st,
+                          const double* pscale = nullptr, int64_t n = 0);
+// out[j][r] = in[j][r] * s[r mod n] for j < n_omega, r < rows (in and out may alias)
+template <typename R>
+cudaError_t launch_scale_block(const void* in, int64_t in_stride, void* out, int64_t out_stride, int n_omega,
+                               int64_t rows, int64_t n, const double* s, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 
 // ----- tensor-core contractions (tc_contract.cu), FP32 mode -----------------

@@ -43,6 +43,9 @@ rsv_status on_frequencies(rsv_operator op);
 // Sets the flag if the state block holds a NaN / Inf (kinds without an in-kernel norm monitor).
 cudaError_t check_finite(rsv_operator op, const void* state, int64_t count, bool real_state);
 cudaError_t state_sq_norms(rsv_operator op, int kg, int64_t n_end, double* d_out);
+// Per-instance squared norms of vector 0 of the state after step n_end; the decay probe's initial state.
+cudaError_t instance_sq_norms(rsv_operator op, int64_t n_end, double* d_out);
+cudaError_t probe_initial_state(rsv_operator op, uint64_t seed);
 
 // dense kind (dense_kernels.cu)
 rsv_status dense_on_frequencies(rsv_operator op);

@@ -551,6 +551,238 @@ cudaError_t launch_adr2d_step(rsv_operator op, const StGeom& g, const R* uin, R*
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// 3-D system, FP32: RK4 in two launches per step, each fusing a pair of stages.
+//
+//   pair A (stages 1, 2):  k1 = A u + f(t_n)        on the tile + 1 halo cell in x, y
+//                          x2 = u + h/2 k1           (shared memory)
+//                          k2 = A x2 + f(t_n + h/2)  on the tile
+//                          x3 = u + h/2 k2,  acc = u + h/6 k1 + h/3 k2,  Y <- u
+//   pair B (stages 3, 4):  k3 = A x3 + f(t_n + h/2)  on the tile + 1 halo cell in x, y
+//                          x4 = u + h k3             (shared memory)
+//                          k4 = A x4 + f(t_n + h)    on the tile
+//                          u' = acc + h/3 k3 + h/6 k4
+// which is the classical RK4 update u + h/6 (k1 + 2 k2 + 2 k3 + k4).  h/6 k1 and h/3 k3
+// are recovered from the stage values in shared memory, (x2 - u)/3 and (x4 - u)/3.
+//
+// A CTA owns a TX x TY tile in (x, y) of one vector and a run of ZC planes in z, and
+// streams through z: the stencil input of the first stage of the pair (u or x3) sits in a
+// ring of four planes with two halo cells in x and y (three planes in use, the next one
+// arriving by asynchronous copies), the intermediate stage (x2 or x4) in a ring of three
+// planes with one halo cell.  At plane p the first stage is evaluated on plane p + 1 and
+// the second on plane p, one barrier apart.  Per step the state-sized arrays cross HBM
+// about 11 times (pair A: u, two forcing samples read, x3 and acc written, plus the
+// snapshot on analysed steps; pair B: x3, u, acc and two forcing samples read, u' written)
+// against about 20 for the four single-stage kernels; halo cells come from L2.
+// Cells outside the grid hold zero (homogeneous Dirichlet), in both rings.
+// ---------------------------------------------------------------------------
+constexpr int k3TX = 64, k3TY = 8, k3ZC = 16;
+constexpr int k3UW = k3TX + 4, k3UH = k3TY + 4;     // ring of the pair's stencil input (halo 2)
+constexpr int k3XW = k3TX + 2, k3XH = k3TY + 2;     // ring of the intermediate stage (halo 1)
+constexpr int k3UP = k3UW * k3UH, k3XP = k3XW * k3XH;
+constexpr int k3Threads = 256;
+constexpr size_t k3Smem = sizeof(float) * (4 * 3 * (size_t)k3UP + 3 * 3 * (size_t)k3XP);
+
+struct Pair3D {
+  const float* in;     // stencil input of the first stage: u (pair A) or x3 (pair B)
+  const float* u;      // pair B: the state u (pair A reads u as `in`)
+  const float* acc;    // pair B: accumulator from pair A
+  const float* fa;     // forcing of the first stage: f(t_n) (A) or f(t_n + h/2) (B); nullable
+  const float* fb;     // forcing of the second stage: f(t_n + h/2) (A) or f(t_n + h) (B); nullable
+  float* out;          // pair A: x3; pair B: u'
+  float* acc_out;      // pair A: accumulator
+  float* ysnap;        // pair A: snapshot of u (nullable)
+  float h;
+};
+
+// 7-point operator (forward or transposed) of component-interleaved planes at local (lx, ly) of a
+// plane with width W, for the cell (i, j, kz) of the grid; x planes: below, centre, above.
+template <bool ADJ, int W, int PLANE>
+__device__ __forceinline__ void op3d_smem(const float* __restrict__ xb, const float* __restrict__ xc,
+                                          const float* __restrict__ xt, int lx, int ly, int i, int64_t q,
+                                          const StGeom& g, float cdx, float idx2, float idy2, float idz2,
+                                          float nu, float out[3]) {
+  const float* U = reinterpret_cast<const float*>(g.f0);
+  const float* Ux = reinterpret_cast<const float*>(g.f1);
+  const float* Uy = reinterpret_cast<const float*>(g.f2);
+  const float* Uz = reinterpret_cast<const float*>(g.f3);
+  const int e = ly * W + lx;
+  float xcen[3];
+  float uw = 0.f, ue = 0.f, uc = 0.f;
+  if (ADJ) {
+    uw = i > 0 ? __ldg(U + q - 1) : 0.f;
+    ue = i < g.nx - 1 ? __ldg(U + q + 1) : 0.f;
+  } else {
+    uc = __ldg(U + q);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* pc = xc + c * PLANE;
+    const float cc = pc[e], w = pc[e - 1], ee = pc[e + 1], s = pc[e - W], n = pc[e + W];
+    const float b = xb[c * PLANE + e], t = xt[c * PLANE + e];
+    xcen[c] = cc;
+    const float adv = ADJ ? (ue * ee - uw * w) * cdx : -uc * (ee - w) * cdx;
+    out[c] = adv + nu * (idx2 * (w + ee - 2.f * cc) + idy2 * (s + n - 2.f * cc) + idz2 * (b + t - 2.f * cc));
+  }
+  const float gx = __ldg(Ux + q), gy = __ldg(Uy + q), gz = __ldg(Uz + q);
+  if (ADJ) {
+    out[0] -= gx * xcen[0];
+    out[1] -= gy * xcen[0];
+    out[2] -= gz * xcen[0];
+  } else {
+    out[0] -= gx * xcen[0] + gy * xcen[1] + gz * xcen[2];
+  }
+}
+
+template <bool ADJ, bool PAIR_B>
+__global__ void __launch_bounds__(k3Threads) adv3d_pair_kernel(StGeom g, Pair3D P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* ring = reinterpret_cast<float*>(smem_raw);            // [4 planes][3 comps][k3UP]
+  float* mid = ring + 4 * 3 * k3UP;                              // [3 planes][3 comps][k3XP]
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int64_t ncell = (int64_t)nx * ny * nz;
+  const int64_t plane = (int64_t)nx * ny;
+  // block order: vector fastest (base-flow fields of a tile shared through L2), then x, y, z
+  int b = blockIdx.x;
+  const int v = b % g.kg;
+  b /= g.kg;
+  const int ntx = (nx + k3TX - 1) / k3TX, nty = (ny + k3TY - 1) / k3TY;
+  const int X0 = (b % ntx) * k3TX;
+  b /= ntx;
+  const int Y0 = (b % nty) * k3TY;
+  const int z0 = (b / nty) * k3ZC;
+  const int z1 = min(z0 + k3ZC, nz);
+  const int64_t base = (int64_t)v * g.n;
+  const float* in = P.in + base;
+  const float cdx = 0.5f / (float)g.dx, idx2 = 1.f / ((float)g.dx * (float)g.dx);
+  const float idy2 = 1.f / ((float)g.dy * (float)g.dy), idz2 = 1.f / ((float)g.dz * (float)g.dz);
+  const float nu = (float)g.visc;
+  const float h = P.h;
+  // stage coefficients: pair A x2 = u + h/2 k1; pair B x4 = u + h k3
+  const float c1 = PAIR_B ? h : 0.5f * h;
+  const float c2 = PAIR_B ? h / 6.f : 0.5f * h;     // pair A: x3 = u + h/2 k2; pair B: u' = ... + h/6 k4
+  const int tid = threadIdx.x;
+
+  // asynchronous copy of plane kz of the stencil input (tile + 2 halo cells) into ring slot kz & 3
+  auto load_plane = [&](int kz) {
+    float* dst = ring + (size_t)(kz & 3) * 3 * k3UP;
+    const bool zin = kz >= 0 && kz < nz;
+    for (int e = tid; e < 3 * k3UP; e += k3Threads) {
+      const int c = e / k3UP, r = e - c * k3UP;
+      const int gi = X0 - 2 + r % k3UW, gj = Y0 - 2 + r / k3UW;
+      if (zin && gi >= 0 && gi < nx && gj >= 0 && gj < ny)
+        cp_async_elem(dst + e, in + c * ncell + (int64_t)kz * plane + (int64_t)gj * nx + gi);
+      else
+        dst[e] = 0.f;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  // first stage of the pair on plane kz, tile + 1 halo cell: x_mid = u + c1 (A x + f_a); zero outside the grid
+  auto first_stage = [&](int kz) {
+    float* dst = mid + (size_t)(kz % 3 + 3) % 3 * 3 * k3XP;
+    const float* xb = ring + (size_t)((kz - 1) & 3) * 3 * k3UP;
+    const float* xc = ring + (size_t)(kz & 3) * 3 * k3UP;
+    const float* xt = ring + (size_t)((kz + 1) & 3) * 3 * k3UP;
+    const bool zin = kz >= 0 && kz < nz;
+    for (int e = tid; e < k3XP; e += k3Threads) {
+      const int lx = e % k3XW, ly = e / k3XW;
+      const int gi = X0 - 1 + lx, gj = Y0 - 1 + ly;
+      float xo[3] = {0.f, 0.f, 0.f};
+      if (zin && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+        const int64_t q = (int64_t)kz * plane + (int64_t)gj * nx + gi;
+        float k[3];
+        op3d_smem<ADJ, k3UW, k3UP>(xb, xc, xt, lx + 1, ly + 1, gi, q, g, cdx, idx2, idy2, idz2, nu, k);
+        const int eu = (ly + 1) * k3UW + lx + 1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int64_t pidx = base + c * ncell + q;
+          const float fv = P.fa ? __ldg(P.fa + pidx) : 0.f;
+          const float uu = PAIR_B ? __ldg(P.u + pidx) : xc[c * k3UP + eu];
+          xo[c] = uu + c1 * (k[c] + fv);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dst[c * k3XP + e] = xo[c];
+    }
+  };
+
+  // second stage of the pair on plane kz, the tile
+  auto second_stage = [&](int kz) {
+    const float* mb = mid + (size_t)((kz - 1) % 3 + 3) % 3 * 3 * k3XP;
+    const float* mc = mid + (size_t)(kz % 3) * 3 * k3XP;
+    const float* mt = mid + (size_t)((kz + 1) % 3) * 3 * k3XP;
+    const float* uc = ring + (size_t)(kz & 3) * 3 * k3UP;
+    for (int e = tid; e < k3TX * k3TY; e += k3Threads) {
+      const int tx = e % k3TX, ty = e / k3TX;
+      const int gi = X0 + tx, gj = Y0 + ty;
+      if (gi >= nx || gj >= ny) continue;
+      const int64_t q = (int64_t)kz * plane + (int64_t)gj * nx + gi;
+      float k[3];
+      op3d_smem<ADJ, k3XW, k3XP>(mb, mc, mt, tx + 1, ty + 1, gi, q, g, cdx, idx2, idy2, idz2, nu, k);
+      const int em = (ty + 1) * k3XW + tx + 1;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int64_t pidx = base + c * ncell + q;
+        const float fv = P.fb ? __ldg(P.fb + pidx) : 0.f;
+        const float xm = mc[c * k3XP + em];
+        if (!PAIR_B) {
+          const float uu = uc[c * k3UP + (ty + 2) * k3UW + tx + 2];
+          const float kk = k[c] + fv;
+          P.out[pidx] = uu + c2 * kk;                                      // x3
+          P.acc_out[pidx] = uu + (xm - uu) * (1.f / 3.f) + (h / 3.f) * kk;  // u + h/6 k1 + h/3 k2
+          if (P.ysnap) P.ysnap[pidx] = uu;
+        } else {
+          const float uu = __ldg(P.u + pidx);
+          const float a = __ldg(P.acc + pidx) + (xm - uu) * (1.f / 3.f);   // + h/3 k3
+          P.out[pidx] = a + c2 * (k[c] + fv);                              // + h/6 k4
+        }
+      }
+    }
+  };
+
+  // prologue: planes z0 - 2 .. z0 + 1 of the stencil input, first stage on plane z0 - 1
+  for (int kz = z0 - 2; kz <= z0 + 1; ++kz) load_plane(kz);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  first_stage(z0 - 1);
+  for (int p = z0 - 1; p < z1; ++p) {
+    // plane p + 2 has landed (the prologue or the previous iteration's copy); the slot of
+    // plane p - 1 is free: it receives plane p + 3 while this iteration computes
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    if (p + 3 <= z1 + 1) load_plane(p + 3);
+    first_stage(p + 1);
+    __syncthreads();
+    if (p >= z0) second_stage(p);
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <bool ADJ, bool PAIR_B>
+cudaError_t launch_pair3d(rsv_operator op, const StGeom& g, const Pair3D& P) {
+  static int attr_dev[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_dev[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(adv3d_pair_kernel<ADJ, PAIR_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)k3Smem);
+    if (e != cudaSuccess) return e;
+    attr_dev[dev] = 1;
+  }
+  const unsigned ntx = (unsigned)((g.nx + k3TX - 1) / k3TX), nty = (unsigned)((g.ny + k3TY - 1) / k3TY);
+  const unsigned ntz = (unsigned)((g.nz + k3ZC - 1) / k3ZC);
+  const unsigned blocks = ntx * nty * ntz * (unsigned)g.kg;
+  adv3d_pair_kernel<ADJ, PAIR_B><<<blocks, k3Threads, k3Smem, op->stream>>>(g, P);
+  return cudaGetLastError();
+}
+
+// RSV_STENCIL3D_STAGED=1 keeps FP32 3-D marches on the four single-stage kernels (comparisons).
+bool adv3d_pairs_enabled() {
+  const char* e = getenv("RSV_STENCIL3D_STAGED");
+  return !(e != nullptr && e[0] == '1');
+}
+
 // RSV_STENCIL_FUSED=1 selects the whole-step kernel (read at each march tile).  The
 // per-stage float4 kernels stay the default: on GB300 they measured 5% faster at the
 // 1024 x 512 x 16 workload although they move more bytes.
@@ -688,6 +920,47 @@ cudaError_t stencil_march_tile(rsv_operator op, const MarchTile& t, void* state,
       std::swap(cur, nxt);
     }
     if (e == cudaSuccess && cur != u) e = cudaMemcpyAsync(u, cur, sizeof(R) * rows, cudaMemcpyDeviceToDevice, op->stream);
+    if (e == cudaSuccess) e = check_finite(op, u, rows, true);
+    return e;
+  }
+  if (sizeof(R) == 4 && op->kind == RSV_OP_ADV3D && adv3d_pairs_enabled()) {
+    // two fused stage pairs per step; the state ping-pongs between u and xb, x3 lives in xa
+    float* cur = reinterpret_cast<float*>(u);
+    float* nxt = reinterpret_cast<float*>(xb);
+    for (int s = 0; s < t.steps && e == cudaSuccess; ++s) {
+      const int64_t n = t.n0 + s;
+      const bool forced = F != nullptr && n < t.n_forced;
+      const float* Fr = static_cast<const float*>(F);
+      Pair3D pa;
+      pa.in = cur;
+      pa.u = nullptr;
+      pa.acc = nullptr;
+      pa.fa = forced ? Fr + (size_t)(2 * s) * rows : nullptr;
+      pa.fb = forced ? Fr + (size_t)(2 * s + 1) * rows : nullptr;
+      pa.out = reinterpret_cast<float*>(xa);
+      pa.acc_out = reinterpret_cast<float*>(acc);
+      pa.ysnap = (Y != nullptr && s >= t.y_first) ? static_cast<float*>(Y) + (size_t)s * rows : nullptr;
+      pa.h = (float)op->h;
+      Pair3D pb = pa;
+      pb.in = reinterpret_cast<const float*>(xa);
+      pb.u = cur;
+      pb.acc = reinterpret_cast<const float*>(acc);
+      pb.fa = pa.fb;
+      pb.fb = forced ? Fr + (size_t)(2 * s + 2) * rows : nullptr;
+      pb.out = nxt;
+      pb.acc_out = nullptr;
+      pb.ysnap = nullptr;
+      if (t.adjoint) {
+        e = launch_pair3d<true, false>(op, g, pa);
+        if (e == cudaSuccess) e = launch_pair3d<true, true>(op, g, pb);
+      } else {
+        e = launch_pair3d<false, false>(op, g, pa);
+        if (e == cudaSuccess) e = launch_pair3d<false, true>(op, g, pb);
+      }
+      std::swap(cur, nxt);
+    }
+    if (e == cudaSuccess && cur != reinterpret_cast<float*>(u))
+      e = cudaMemcpyAsync(u, cur, sizeof(float) * rows, cudaMemcpyDeviceToDevice, op->stream);
     if (e == cudaSuccess) e = check_finite(op, u, rows, true);
     return e;
   }

@@ -49,7 +49,8 @@ class rsv_operator_desc(ctypes.Structure):
 class rsv_march_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("n_transient_windows", ctypes.c_int32),
                 ("tail_steps", ctypes.c_int64), ("tile_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("tail_tol", ctypes.c_double)]
+                ("tail_tol", ctypes.c_double), ("decay_tol", ctypes.c_double), ("decay_max_steps", ctypes.c_int64),
+                ("decay_seed", ctypes.c_uint64)]
 
 
 _lib = None
@@ -73,6 +74,20 @@ _ENTRY_POINTS = {
     "rsv_gains_modes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.POINTER(rsv_march_opts),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p]),
+    "rsv_set_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "rsv_decay_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int64,
+                                       ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "rsv_refine_gains": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(rsv_march_opts), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "rsv_arnoldi_gains": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(rsv_march_opts), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "rsv_orthonormalize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_double)]),
     "rsv_apply_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_void_p]),
     "rsv_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
@@ -122,9 +137,11 @@ def _ptr(x) -> int:
     raise TypeError(type(x))
 
 
-def _opts(variant="ssrm", n_transient_windows=0, tail_steps=0, tile_steps=0, tail_tol=0.0):
+def _opts(variant="ssrm", n_transient_windows=0, tail_steps=0, tile_steps=0, tail_tol=0.0, decay_tol=0.0,
+          decay_max_steps=0, decay_seed=0):
     return rsv_march_opts(RSV_SSRM if variant == "ssrm" else RSV_TRM, int(n_transient_windows),
-                          int(tail_steps), int(tile_steps), 0, float(tail_tol))
+                          int(tail_steps), int(tile_steps), 0, float(tail_tol), float(decay_tol),
+                          int(decay_max_steps), int(decay_seed))
 
 
 class Operator:
@@ -200,6 +217,57 @@ def rsv_gains_modes(op: Operator, omega_block, k: int, n_power_iter: int, n_mode
                                 ctypes.byref(o), gains.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                 _ptr(forcing_modes), _ptr(response_modes)))
     return gains
+
+
+def rsv_set_weights(op: Operator, b=None, c=None, w_f=None, w_y=None):
+    """Diagonal forcing / observation matrices and metrics (host arrays of n doubles, None = identity)."""
+    arrs = [None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.float64)) for x in (b, c, w_f, w_y)]
+    ptrs = [None if x is None else x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for x in arrs]
+    _check(_lib.rsv_set_weights(op.handle, *ptrs))
+
+
+def rsv_decay_probe(op: Operator, tol: float, max_steps: int, seed: int = 0, check_every: int = 0,
+                    adjoint: bool = False):
+    """(steps, ratio) of the decay run; raises RsvError (UNSTABLE) for a growing or non-decaying system."""
+    st, r = ctypes.c_int64(), ctypes.c_double()
+    _check(_lib.rsv_decay_probe(op.handle, int(bool(adjoint)), float(tol), int(max_steps), int(seed),
+                                int(check_every), ctypes.byref(st), ctypes.byref(r)))
+    return st.value, r.value
+
+
+def rsv_refine_gains(op: Operator, basis, k: int, n_modes: int, gains: np.ndarray, forcing_modes=None,
+                     response_modes=None, **opts):
+    """Rayleigh-Ritz refinement on `basis`; gains: host float64 [n_instances][n_omega][n_modes], filled in place."""
+    if gains.dtype != np.float64 or not gains.flags.c_contiguous:
+        raise ValueError("gains must be a C-contiguous float64 array")
+    o = _opts(**opts)
+    _check(_lib.rsv_refine_gains(op.handle, _ptr(basis), int(k), int(n_modes), ctypes.byref(o),
+                                 gains.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(forcing_modes),
+                                 _ptr(response_modes)))
+    return gains
+
+
+def rsv_arnoldi_gains(op: Operator, f0, m: int, n_modes: int, gains: np.ndarray, forcing_modes=None,
+                      response_modes=None, **opts):
+    """Arnoldi gains from start vectors f0 [n_omega][1][n]; gains: host float64 [n_instances][n_omega][n_modes]."""
+    if gains.dtype != np.float64 or not gains.flags.c_contiguous:
+        raise ValueError("gains must be a C-contiguous float64 array")
+    o = _opts(**opts)
+    _check(_lib.rsv_arnoldi_gains(op.handle, _ptr(f0), int(m), int(n_modes), ctypes.byref(o),
+                                  gains.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(forcing_modes),
+                                  _ptr(response_modes)))
+    return gains
+
+
+def rsv_orthonormalize(op: Operator, block, k: int, r_factor: np.ndarray | None = None):
+    """CholeskyQR2 of `block` in place; r_factor: optional host complex128 [n_omega][n_instances][k][k]."""
+    rp = None
+    if r_factor is not None:
+        if r_factor.dtype != np.complex128 or not r_factor.flags.c_contiguous:
+            raise ValueError("r_factor must be a C-contiguous complex128 array")
+        rp = r_factor.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(_lib.rsv_orthonormalize(op.handle, _ptr(block), int(k), rp))
+    return r_factor
 
 
 def rsv_apply_operator(op: Operator, x, k: int, adjoint: bool, y):

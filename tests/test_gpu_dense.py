@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from parity import gain_rel, rel_rows
 from oracle import frequencies, march, resolvent, rsvd
 
 pytestmark = pytest.mark.gpu
@@ -33,8 +34,6 @@ def _dev(x, prec):
     return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dt)
 
 
-def _relerr(a, b):
-    return float(np.abs(a - b).max() / np.abs(b).max())
 
 
 def _oracle(w, a, fh, adjoint=False):
@@ -54,7 +53,7 @@ def test_dense_apply(rsv, prec, adjoint):
         y = _dev(x, prec) * 0
         rsv.rsv_apply_operator(op, _dev(x, prec), 5, adjoint, y)
         ref = ((a.conj().T if adjoint else a) @ x.T).T
-        assert _relerr(y.cpu().numpy(), ref) < (1e-13 if prec == 0 else 1e-6)
+        assert rel_rows(y.cpu().numpy(), ref) < (1e-13 if prec == 0 else 1e-6)
     finally:
         rsv.rsv_destroy_operator(op)
 
@@ -71,7 +70,7 @@ def test_dense_march_fp64(rsv, variant, tile, adjoint):
         y = x * 0
         f = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
         f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=tile))
-        assert _relerr(y.cpu().numpy(), _oracle(w, a, fh, adjoint)) < TOL64
+        assert rel_rows(y.cpu().numpy(), _oracle(w, a, fh, adjoint)) < TOL64
     finally:
         rsv.rsv_destroy_operator(op)
 
@@ -89,7 +88,7 @@ def test_dense_march_fp32(rsv, adjoint, contract, monkeypatch):
         y = x * 0
         f = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
         f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=128))
-        assert _relerr(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh, adjoint)) < TOL32_MARCH
+        assert rel_rows(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh, adjoint)) < TOL32_MARCH
     finally:
         rsv.rsv_destroy_operator(op)
 
@@ -106,7 +105,7 @@ def test_dense_rsvd_fp64(rsv):
         kw = dict(variant=w.variant, n_trans=w.n_transient_windows, tail_steps=w.tail_steps)
         rg, _, _ = rsvd.block_rsvd(lambda b: march.march(a, g, b, **kw),
                                    lambda b: march.march(a, g, b, adjoint=True, **kw), fh, w.n_power_iter, 3)
-        assert np.abs(gains - rg).max() / rg.max() < TOL64
+        assert gain_rel(gains, rg) < TOL64
     finally:
         rsv.rsv_destroy_operator(op)
 
@@ -145,7 +144,7 @@ def test_dense_full_size_sampled(rsv):
         j = 100
         rh = resolvent.rk4_discrete(a, w.omegas[j], h)
         ref = (rh @ fh[j].astype(np.complex64).astype(np.complex128).T).T
-        assert _relerr(y[j].cpu().numpy().astype(np.complex128), ref) < 1e-4
+        assert rel_rows(y[j].cpu().numpy().astype(np.complex128), ref) < 1e-4
     finally:
         rsv.rsv_destroy_operator(op)
 
@@ -168,7 +167,7 @@ def test_dense_tensor_core_step(rsv, n, x_half, adjoint, path, k, monkeypatch):
         y = x * 0
         f = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
         f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=200))
-        assert _relerr(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh, adjoint)) < TOL32_MARCH
+        assert rel_rows(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh, adjoint)) < TOL32_MARCH
     finally:
         rsv.rsv_destroy_operator(op)
 
@@ -186,6 +185,6 @@ def test_dense_fp32_size_outside_tensor_tiles(rsv):
         x = _dev(fh, 1)
         y = x * 0
         rsv.rsv_march_direct(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=200))
-        assert _relerr(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh)) < TOL32_MARCH
+        assert rel_rows(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh)) < TOL32_MARCH
     finally:
         rsv.rsv_destroy_operator(op)

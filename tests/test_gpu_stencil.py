@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from parity import gain_rel, rel_rows
 from oracle import frequencies, march, operators, rsvd
 
 pytestmark = pytest.mark.gpu
@@ -25,8 +26,6 @@ def _dev(x, prec):
                                                         dtype=torch.complex128 if prec == 0 else torch.complex64)
 
 
-def _relerr(a, b):
-    return float(np.abs(a - b).max() / np.abs(b).max())
 
 
 def _adr_small(variant="ssrm", omegas=None, k=3):
@@ -85,7 +84,7 @@ def test_stencil_apply(rsv, make, prec, adjoint):
         rsv.rsv_apply_operator(op, _dev(x, prec), 3, adjoint, y)
         a = _matrix(w)
         ref = ((a.T if adjoint else a) @ x.T).T
-        assert _relerr(y.cpu().numpy(), ref) < (1e-13 if prec == 0 else 1e-5)
+        assert rel_rows(y.cpu().numpy(), ref) < (1e-13 if prec == 0 else 1e-5)
     finally:
         rsv.rsv_destroy_operator(op)
 
@@ -104,7 +103,7 @@ def test_stencil_march_fp64(rsv, make, variant, tile, adjoint):
         f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=tile))
         ref = _oracle(w, _matrix(w), fh, adjoint)
         got = y.cpu().numpy()
-        assert _relerr(got, ref) < TOL64
+        assert rel_rows(got, ref) < TOL64
         assert np.abs(got[0].imag).max() == 0.0   # w = 0 response of a real system is real
     finally:
         rsv.rsv_destroy_operator(op)
@@ -125,7 +124,7 @@ def test_stencil_march_fp32(rsv, make, adjoint, contract, monkeypatch):
         f = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
         f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=16))
         ref = _oracle(w, _matrix(w), fh, adjoint)
-        assert _relerr(y.cpu().numpy().astype(np.complex128), ref) < TOL32
+        assert rel_rows(y.cpu().numpy().astype(np.complex128), ref) < TOL32
     finally:
         rsv.rsv_destroy_operator(op)
 
@@ -144,7 +143,7 @@ def test_stencil_rsvd_fp64(rsv, make):
         rg, _, _ = rsvd.block_rsvd(lambda b: march.march(a, g, b, **kw),
                                    lambda b: march.march(a, g, b, adjoint=True, **kw), fh, 1, 2,
                                    real_rows=[j for j, om in enumerate(w.omegas) if om == 0.0])
-        assert np.abs(gains - rg).max() / rg.max() < TOL64
+        assert gain_rel(gains, rg) < TOL64
     finally:
         rsv.rsv_destroy_operator(op)
 
@@ -171,7 +170,7 @@ def test_stencil_full_grid_fp32_vs_fp64(rsv, make):
             torch.cuda.empty_cache()
         finally:
             rsv.rsv_destroy_operator(op)
-    assert _relerr(outs[1], outs[0]) < 1e-4
+    assert rel_rows(outs[1], outs[0]) < 1e-4
 
 
 @pytest.mark.parametrize("make", [_adr_small, _adr_multi])
@@ -193,6 +192,36 @@ def test_adr2d_step_paths(rsv, make, prec, adjoint, path, monkeypatch):
         f = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
         f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=15))
         ref = _oracle(w, _matrix(w), fh, adjoint)
-        assert _relerr(y.cpu().numpy().astype(np.complex128), ref) < (TOL64 if prec == 0 else TOL32)
+        assert rel_rows(y.cpu().numpy().astype(np.complex128), ref) < (TOL64 if prec == 0 else TOL32)
+    finally:
+        rsv.rsv_destroy_operator(op)
+
+
+def _adv_multi(variant="trm", k=2):
+    """Several fused-pair tiles in x and y (64 x 8), ragged, and two z chunks (16 + 4 planes)."""
+    sysm = W.ADV3D(nx=70, ny=11, nz=20, lx=20.0, ly=10.0, lz=10.0, visc=0.02)
+    om = np.array([0.04 * np.pi * 5 * j for j in range(6)])
+    dx = sysm.lx / (sysm.nx + 1)
+    return W.Workload("adv_multi", sysm, om, 0.5 * dx, k, variant, n_transient_windows=1, tail_steps=30,
+                      n_power_iter=1, real_state=True, seed=W.SEED_BASE + 45)
+
+
+@pytest.mark.parametrize("make", [_adv_small, _adv_multi])
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("path", ["pairs", "staged"])
+def test_adv3d_step_paths(rsv, make, adjoint, path, monkeypatch):
+    """FP32 3-D march with the two fused stage-pair kernels per step (z-streaming, shared-memory
+    rings) and with the four single-stage kernels, vs the oracle, on grids with ragged tiles."""
+    monkeypatch.setenv("RSV_STENCIL3D_STAGED", "1" if path == "staged" else "0")
+    w = make("trm")
+    op = rsv.create_for_workload(w, 1)
+    try:
+        fh = W.test_block(w).astype(np.complex64).astype(np.complex128)
+        x = _dev(fh, 1)
+        y = x * 0
+        f = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
+        f(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=15))
+        ref = _oracle(w, _matrix(w), fh, adjoint)
+        assert rel_rows(y.cpu().numpy().astype(np.complex128), ref) < TOL32
     finally:
         rsv.rsv_destroy_operator(op)

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from parity import gain_rel, rel_rows
 from oracle import frequencies, march, operators
 
 pytestmark = pytest.mark.gpu
@@ -25,8 +26,6 @@ def _dev(x, prec):
                                                         dtype=torch.complex128 if prec == 0 else torch.complex64)
 
 
-def _relerr(a, b):
-    return float(np.abs(a - b).max() / np.abs(b).max())
 
 
 def _case(kind):
@@ -66,7 +65,7 @@ def test_trm_norm_truncated_tail(rsv, kind, prec, adjoint):
                                  tail_tol=tol, check_every=tile, return_steps=True)
         assert g.n_t <= steps < g.n_t + cap           # the rule ended the tail before the cap
         assert int(desc["steps"]) == steps
-        assert _relerr(y.cpu().numpy().astype(np.complex128), ref) < TOL[prec]
+        assert rel_rows(y.cpu().numpy().astype(np.complex128), ref) < TOL[prec]
     finally:
         rsv.rsv_destroy_operator(op)
 

@@ -71,6 +71,21 @@ def test_decay_steps_normal_matrix_closed_form():
     assert steps == _closed_form_steps(lam, q.conj().T @ u0, h, tol, 4)
 
 
+def test_decay_steps_per_instance_closed_form():
+    """A batched system decays only when every block has: the slowest block sets the length, even
+    when its share of the total norm is small."""
+    lam_a = np.array([-0.5 + 0.2j, -0.8])          # fast block
+    lam_b = np.array([-0.03 + 0.1j])               # slow block
+    a = np.diag(np.concatenate([lam_a, lam_b]))
+    u0 = np.array([1.0, 1.0, 1e-3])                 # the slow block starts small
+    h, tol = 0.1, 1e-6
+    steps, _, status = decay.decay_probe(a, h, u0, tol, 10 ** 6, 5, instances=[(0, 2), (2, 1)])
+    assert status == "decayed"
+    assert steps == max(_closed_form_steps(lam_a, u0[:2], h, tol, 5), _closed_form_steps(lam_b, u0[2:], h, tol, 5))
+    whole, _, _ = decay.decay_probe(a, h, u0, tol, 10 ** 6, 5)
+    assert whole < steps                            # the whole-vector ratio would stop too early
+
+
 def test_decay_probe_reports_growth_and_cap():
     grow = np.diag([0.05, -0.3])
     steps, ratio, status = decay.decay_probe(grow, 0.1, np.array([1.0, 1.0]), 1e-6, 10 ** 6, 10)
