@@ -62,6 +62,12 @@ typedef enum {
 } rsv_precision;
 
 typedef enum {
+  RSV_SCHEME_RK4 = 0, /* classical 4-stage Runge-Kutta, forcing at t_n, t_n + h/2, t_n + h      */
+  RSV_SCHEME_CN = 1   /* Crank-Nicolson (I - hA/2) u' = (I + hA/2) u + h/2 (f(t_n) + f(t_n + h)),
+                         second order, GL1D only (Sec. 3)                                   */
+} rsv_scheme;
+
+typedef enum {
   RSV_SSRM = 0,      /* steady-state response: periodic forcing (Sec. 2.3)          */
   RSV_TRM = 1        /* transient response: one forcing window + decay tail (Sec. 2.2) */
 } rsv_variant;
@@ -73,7 +79,7 @@ typedef struct {
   int32_t precision;         /* rsv_precision                                        */
   double dt;                 /* target step; the march uses h = T / ceil(T / dt)     */
 
-  /* RSV_OP_GL1D: du/dt = -nu u_x + gamma u_xx + mu(x) u, mu = mu0 + mu_shift + mu2 x^2,
+  /* RSV_OP_GL1D: du/dt = -nu u_x + gamma u_xx + mu(x) u, mu = mu0 + mu_shift + mu1 x + mu2 x^2,
    * on x in (x0, x1); instance i has gl_n[i] points and its own mu0 (Sec. 3,
    * Eq. (GL_timeDomain) family).  Instances are independent diagonal blocks. */
   int32_t n_instances;
@@ -102,6 +108,12 @@ typedef struct {
   double kappa, jet_delta, sponge_amp;
   int32_t sponge_cells;
   double delta0, delta1;
+
+  /* RSV_OP_GL1D: linear term of mu(x) (the paper's Sec. 3 case has mu linear in x). */
+  double mu1;
+  /* Time scheme (rsv_scheme): classical RK4 for every kind, or Crank-Nicolson
+   * for RSV_OP_GL1D (the scheme of the paper's Sec. 3 validation case). */
+  int32_t scheme;
 } rsv_operator_desc;
 
 typedef struct {

@@ -61,6 +61,22 @@ def rk4_step(a, u, h, f0, fh, f1):
     return u + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
 
 
+def cn_factor(a, h):
+    """Crank-Nicolson matrices of du/dt = A u + f: the LU factors of (I - h/2 A) and (I + h/2 A)."""
+    import scipy.sparse as sps
+    import scipy.sparse.linalg as spla
+    n = a.shape[0]
+    eye = sps.identity(n, dtype=np.complex128, format="csc")
+    asp = sps.csc_matrix(a, dtype=np.complex128)
+    return spla.splu((eye - 0.5 * h * asp).tocsc()), (eye + 0.5 * h * asp).tocsr()
+
+
+def cn_step(lu_rhs, u, h, f0, f1):
+    """One Crank-Nicolson step: (I - h/2 A) u' = (I + h/2 A) u + h/2 (f(t_n) + f(t_n + h)) (Sec. 3)."""
+    lu, rhs_m = lu_rhs
+    return lu.solve(rhs_m @ u + 0.5 * h * (f0 + f1))
+
+
 def schedule(grid, variant, n_trans=0, tail_steps=0):
     """(total steps, first analysed step, steps with forcing)."""
     if variant == "ssrm":
@@ -73,10 +89,11 @@ def schedule(grid, variant, n_trans=0, tail_steps=0):
 
 def march(a, grid, fhat, *, variant="ssrm", n_trans=0, tail_steps=0, adjoint=False,
           real_state=False, return_state=False, stop_after=None, tail_tol=0.0, check_every=None,
-          return_steps=False):
+          return_steps=False, scheme="rk4"):
     """Direct (adjoint=False) or adjoint run; returns yhat [n_omega][k][n].
 
     `a` is the system matrix (sparse or dense); the adjoint run uses a^H.
+    `scheme`: "rk4" (classical RK4) or "cn" (Crank-Nicolson, forcing at the step ends).
     `stop_after` ends the march early (for timing a bounded sample only).
     `tail_tol`, `check_every`: TRM truncation by the state norm (see the module
     docstring).  `return_steps` also returns the number of steps marched.
@@ -97,17 +114,18 @@ def march(a, grid, fhat, *, variant="ssrm", n_trans=0, tail_steps=0, adjoint=Fal
     peak = np.zeros(kk)
     last = total if stop_after is None else min(total, stop_after)
     marched = 0
+    cn = cn_factor(op, h) if scheme == "cn" else None
     for step in range(last):
         t = step * h
         if step >= first:
             acc += np.exp(-1j * om * t)[:, None, None] * u.T[None, :, :]
         if step < forced:
             f0 = synthesize(fhat, om, t, real_state, weights)
-            fh = synthesize(fhat, om, t + 0.5 * h, real_state, weights)
+            fh = synthesize(fhat, om, t + 0.5 * h, real_state, weights) if cn is None else None
             f1 = synthesize(fhat, om, t + h, real_state, weights)
         else:
             f0 = fh = f1 = zero
-        u = rk4_step(op, u, h, f0, fh, f1)
+        u = rk4_step(op, u, h, f0, fh, f1) if cn is None else cn_step(cn, u, h, f0, f1)
         marched = step + 1
         if adaptive and (marched % check_every == 0 or marched == total):
             norms = np.sqrt(np.sum(np.abs(u) ** 2, axis=0))

@@ -15,7 +15,8 @@ from scipy.special import erf
 
 
 def gl1d(sysm) -> sps.csr_matrix:
-    """Linearised GL (Sec. 3 Eq. (GL_timeDomain) family): -nu u_x + gamma u_xx + mu(x) u.
+    """Linearised GL (Sec. 3 Eq. (GL_timeDomain) family): -nu u_x + gamma u_xx + mu(x) u,
+    mu(x) = mu0 + mu_shift + mu1 x + mu2 x^2.
 
     Central differences u_x ~ (u[i+1] - u[i-1]) / (2 dx),
     u_xx ~ (u[i+1] - 2 u[i] + u[i-1]) / dx^2, Dirichlet zero outside the
@@ -27,7 +28,7 @@ def gl1d(sysm) -> sps.csr_matrix:
         rows, cols, vals = [], [], []
         for i in range(n):
             x = sysm.x0 + (i + 1) * dx
-            mu = mu0 + sysm.mu_shift + sysm.mu2 * x * x
+            mu = mu0 + sysm.mu_shift + getattr(sysm, "mu1", 0.0) * x + sysm.mu2 * x * x
             rows.append(i); cols.append(i); vals.append(-2.0 * sysm.gamma / dx ** 2 + mu)
             if i > 0:
                 rows.append(i); cols.append(i - 1)

@@ -41,6 +41,19 @@ def rk4_discrete(a, omega, h):
     return np.linalg.solve(z * eye - m, (h / 6.0) * g)
 
 
+def cn_discrete(a, omega, h):
+    """Exact steady-state map of the Crank-Nicolson scheme with forcing a e^{i w t} at the step ends:
+    u_{n+1} = M u_n + (h/2) L^{-1} (a_n + a_{n+1}), L = I - hA/2, M = L^{-1}(I + hA/2), and
+    u_n = uhat e^{i w t_n} gives R_h^CN(w) = (z I - M)^{-1} L^{-1} (h/2)(1 + z), z = e^{i w h}."""
+    a = np.asarray(a.todense() if hasattr(a, "todense") else a, dtype=np.complex128)
+    n = a.shape[0]
+    eye = np.eye(n)
+    lmat = eye - 0.5 * h * a
+    m = np.linalg.solve(lmat, eye + 0.5 * h * a)
+    z = np.exp(1j * omega * h)
+    return np.linalg.solve(z * eye - m, np.linalg.solve(lmat, 0.5 * h * (1 + z) * eye))
+
+
 def gains(r, n_modes=None):
     sv = np.linalg.svd(r, compute_uv=False)
     return sv if n_modes is None else sv[:n_modes]

@@ -225,6 +225,8 @@ struct TcMarchArgs {
   int y_first;
   int n, kg, cs, chains;
   int* err;
+  uint64_t wait_ns;         // limit of each wait on another CTA's counter
+  int stall;                // test hook: the first state wait of the tile targets a count nobody reaches
 };
 
 __device__ __forceinline__ void chain_bar(int chain) {
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
     tc::bulk_g2s(A_hi, at, 4 * kATileFloats, &bars[0]);
     tc::bulk_g2s(A_lo, at + kATileFloats, 4 * kATileFloats, &bars[0]);
   }
-  bool ok = tc::mbar_wait(&bars[0], 0, 0xFFFFFFFFu, errv);
+  bool ok = tc::mbar_wait(&bars[0], 0, 0xFFFFFFFFu);   // this CTA's own copy: never abandoned early
   __syncthreads();
   if (chain < a.chains) {
     float* X_sm = Xs + (size_t)chain * kXcFloats;
@@ -333,9 +335,9 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
       }
       // 1. the state slice of this step
       if (ctid == 0) {
-        const int target = a.cs * (int)(n + 1);
-        const bool got = tc::spin_until_geq(&ready[2 * j], target, errv) &&
-                         tc::spin_until_geq(&ready[2 * j + 1], target, errv);
+        const int target = a.cs * (int)(n + 1) + ((a.stall && s == 0) ? (1 << 30) : 0);
+        const bool got = tc::spin_until_geq(&ready[2 * j], target, errv, a.wait_ns) &&
+                         tc::spin_until_geq(&ready[2 * j + 1], target, errv, a.wait_ns);
         if (!got) {
           atomicExch(a.err, 2);
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar_x)) : "memory");
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
       }
       // 2. products
       if (ctid == 0) {
-        bool okx = tc::mbar_wait(bar_x, (uint32_t)(s & 1), 0xFFFFFFFFu, errv) && *errv == 0;
+        bool okx = tc::mbar_wait(bar_x, (uint32_t)(s & 1), 0xFFFFFFFFu) && *errv == 0;
         tc::tc_fence_after();
         if (okx) {
 #pragma unroll 4
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar_m)) : "memory");
         }
       }
-      ok = tc::mbar_wait(bar_m, (uint32_t)(s & 1), 0xFFFFFFFFu, errv) && ok && *errv == 0;
+      ok = tc::mbar_wait(bar_m, (uint32_t)(s & 1), 0xFFFFFFFFu) && ok && *errv == 0;
       tc::tc_fence_after();
       // 3. partial: hi*hi + hi*lo + lo*hi, one row per thread
       float* pb = partg + (((size_t)par * MB + mb) * a.cs + j) * kPartFloats;
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
       //    partial (rpc real-part rows and rpc imaginary-part rows) come in by bulk copies
       const float* pbase = partg + ((size_t)par * MB + mb) * a.cs * kPartFloats;
       if (ctid == 0) {
-        if (!tc::spin_until_geq(&cnt[par * MB + mb], a.cs * (int)((n >> 1) + 1), errv)) {
+        if (!tc::spin_until_geq(&cnt[par * MB + mb], a.cs * (int)((n >> 1) + 1), errv, a.wait_ns)) {
           atomicExch(a.err, 2);
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar_g)) : "memory");
         } else {
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(kMarchThreads, 1) dense_tc_march_kernel(TcMarc
           }
         }
       }
-      if (!tc::mbar_wait(bar_g, (uint32_t)(s & 1), 0xFFFFFFFFu, errv)) atomicExch(a.err, 2);
+      if (!tc::mbar_wait(bar_g, (uint32_t)(s & 1), 0xFFFFFFFFu)) atomicExch(a.err, 2);
       cpx<float>* Ys = (a.Y != nullptr && s >= a.y_first) ? a.Y + (size_t)s * rows : nullptr;
       float* xo_par = Xg + (size_t)(1 - par) * xset;
 #pragma unroll
@@ -584,6 +586,8 @@ cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n
   a.cs = cs;
   a.chains = (kg + kChainVec - 1) / kChainVec;
   a.err = op->d_flag;
+  a.wait_ns = op->wait_limit_ns;
+  a.stall = op->test_stall_wait ? 1 : 0;
   cudaError_t e = cudaSuccess;
   if (n0 == 0) {
     e = cudaMemsetAsync(op->d_ready, 0, sizeof(int) * kMaxChains * 3 * MB, op->stream);

@@ -1,4 +1,4 @@
-// RK4 march of 1-D three-point (tridiagonal) operators: the linearised
+// RK4 and Crank-Nicolson marches of 1-D three-point (tridiagonal) operators: the linearised
 // Ginzburg-Landau family of Sec. 3, Eq. (GL_timeDomain), discretised with
 // central differences, one or many independent instances.
 //
@@ -166,6 +166,131 @@ __global__ void __launch_bounds__(MAXT) gl1d_tile_kernel(Gl1dTile t, cpx<R>* __r
   }
 }
 
+// Crank-Nicolson tile kernel (the time scheme of the paper's Sec. 3 case):
+//   (I - h/2 A) u_{n+1} = (I + h/2 A) u_n + h/2 (f(t_n) + f(t_n + h)).
+// The right-hand side d is formed in registers (one neighbour exchange through shared memory);
+// the constant tridiagonal system is solved by parallel cyclic reduction: at level l (distance
+// s = 2^l) every point eliminates its neighbours at -s and +s,
+//   d_i <- d_i - cl_i^l d_{i-s} - cu_i^l d_{i+s},
+// with factors cl, cu precomputed in FP64 on the host for the step h, and after
+// ceil(log2 max_n) levels u_i = d_i / b_i (inverse pivots precomputed too).  One barrier per level.
+template <typename R, int PPT, int MAXT>
+__global__ void __launch_bounds__(MAXT) gl1d_cn_tile_kernel(Gl1dTile t, cpx<R>* __restrict__ u,
+                                                            const cpx<R>* __restrict__ F, cpx<R>* __restrict__ Y,
+                                                            double* __restrict__ norms, int* __restrict__ flag) {
+  extern __shared__ unsigned char smem_raw[];
+  const int inst = blockIdx.x;
+  const int v = blockIdx.y;
+  const int64_t off = t.inst_off[inst];
+  const int len = (int)(t.inst_off[inst + 1] - off);
+  cpx<R>* sx = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][max_n]
+  const cpx<R>* lo = reinterpret_cast<const cpx<R>*>(t.lo);
+  const cpx<R>* di = reinterpret_cast<const cpx<R>*>(t.di);
+  const cpx<R>* up = reinterpret_cast<const cpx<R>*>(t.up);
+  const cpx<R>* cl = reinterpret_cast<const cpx<R>*>(t.cr_lo);
+  const cpx<R>* cu = reinterpret_cast<const cpx<R>*>(t.cr_up);
+  const cpx<R>* inv = reinterpret_cast<const cpx<R>*>(t.cr_inv);
+  const cpx<R> zero = mk<R>(0, 0);
+  const int64_t rows = (int64_t)t.kg * t.n;
+  const int64_t rbase = (int64_t)v * t.n + off;
+  cpx<R> clo[PPT], cdi[PPT], cup[PPT], us[PPT], pinv[PPT];
+  bool ok[PPT];
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) {
+    const int i = threadIdx.x + m * blockDim.x;
+    ok[m] = i < len;
+    clo[m] = cdi[m] = cup[m] = us[m] = pinv[m] = zero;
+    if (ok[m]) {
+      clo[m] = lo[off + i];
+      cdi[m] = di[off + i];
+      cup[m] = up[off + i];
+      pinv[m] = inv[off + i];
+      us[m] = u[rbase + i];
+    }
+  }
+  const R hh = R(0.5) * R(t.h);
+  int buf = 0;
+  cpx<R> f0[PPT], f1[PPT];
+  const bool forced0 = F != nullptr && t.n0 < t.n_forced;
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) f0[m] = (forced0 && ok[m]) ? F[rbase + threadIdx.x + m * blockDim.x] : zero;
+  for (int s = 0; s < t.steps; ++s) {
+    const bool forced = F != nullptr && t.n0 + s < t.n_forced;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      f1[m] = (forced && ok[m]) ? F[(int64_t)(2 * s + 2) * rows + rbase + threadIdx.x + m * blockDim.x] : zero;
+      if (!forced) f0[m] = zero;
+    }
+    if (Y != nullptr && s >= t.y_first) {
+#pragma unroll
+      for (int m = 0; m < PPT; ++m)
+        if (ok[m]) Y[(int64_t)s * rows + rbase + threadIdx.x + m * blockDim.x] = us[m];
+    }
+    // d = u + h/2 (A u + f0 + f1)
+    cpx<R>* sb = sx + buf * t.max_n;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m)
+      if (ok[m]) sb[threadIdx.x + m * blockDim.x] = us[m];
+    __syncthreads();
+    cpx<R> d[PPT];
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      const int i = threadIdx.x + m * blockDim.x;
+      cpx<R> a = f0[m] + f1[m];
+      if (ok[m]) {
+        if (i > 0) cfma(a, clo[m], sb[i - 1]);
+        cfma(a, cdi[m], us[m]);
+        if (i + 1 < len) cfma(a, cup[m], sb[i + 1]);
+      }
+      d[m] = ok[m] ? us[m] + hh * a : zero;
+    }
+    buf ^= 1;
+    // cyclic reduction of (I - h/2 A) u' = d
+    for (int l = 0; l < t.cr_levels; ++l) {
+      const int sd = 1 << l;
+      cpx<R>* sl = sx + buf * t.max_n;
+#pragma unroll
+      for (int m = 0; m < PPT; ++m)
+        if (ok[m]) sl[threadIdx.x + m * blockDim.x] = d[m];
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < PPT; ++m) {
+        const int i = threadIdx.x + m * blockDim.x;
+        if (!ok[m]) continue;
+        const int64_t k = (int64_t)l * t.n + off + i;
+        cpx<R> r = d[m];
+        if (i - sd >= 0) r = r - cl[k] * sl[i - sd];
+        if (i + sd < len) r = r - cu[k] * sl[i + sd];
+        d[m] = r;
+      }
+      buf ^= 1;
+    }
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      us[m] = pinv[m] * d[m];
+      f0[m] = f1[m];
+    }
+  }
+  double nrm = 0.0;
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) {
+    if (ok[m]) {
+      u[rbase + threadIdx.x + m * blockDim.x] = us[m];
+      nrm += (double)us[m].re * (double)us[m].re + (double)us[m].im * (double)us[m].im;
+    }
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    if (norms != nullptr) norms[(int64_t)v * t.n_inst + inst] = tot;
+    if (!(tot < 1e300)) atomicExch(flag, 1);
+  }
+}
+
 template <typename R>
 __global__ void gl1d_apply_kernel(Gl1dTile t, const cpx<R>* __restrict__ x, cpx<R>* __restrict__ y,
                                   const int32_t* __restrict__ inst_of_point) {
@@ -189,9 +314,16 @@ template <typename R, int PPT, int MAXT>
 cudaError_t launch_ppt(const Gl1dTile& t, int threads, void* u, const void* F, void* Y, double* norms, int* flag,
                        cudaStream_t st) {
   const size_t smem = sizeof(cpx<R>) * 2 * (size_t)(t.max_n + 2);
+  dim3 grid((unsigned)t.n_inst, (unsigned)t.kg);
+  if (t.cr_levels > 0) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(gl1d_cn_tile_kernel<R, PPT, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    gl1d_cn_tile_kernel<R, PPT, MAXT><<<grid, threads, smem, st>>>(t, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y,
+                                                                    norms, flag);
+    return cudaGetLastError();
+  }
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(gl1d_tile_kernel<R, PPT, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((unsigned)t.n_inst, (unsigned)t.kg);
   gl1d_tile_kernel<R, PPT, MAXT><<<grid, threads, smem, st>>>(t, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y, norms,
                                                                flag);
   return cudaGetLastError();

@@ -61,7 +61,7 @@ rsv_status build_gl1d(rsv_operator op, const rsv_operator_desc* d) {
     const double dx = (d->x1 - d->x0) / (double)(n + 1);
     for (int p = 0; p < n; ++p) {
       const double x = d->x0 + (p + 1) * dx;
-      const double mu = d->gl_mu0[i] + d->mu_shift + d->mu2 * x * x;
+      const double mu = d->gl_mu0[i] + d->mu_shift + d->mu1 * x + d->mu2 * x * x;
       lo[off + p] = (p > 0) ? nu / (2.0 * dx) + ga / (dx * dx) : 0.0;
       up[off + p] = (p < n - 1) ? -nu / (2.0 * dx) + ga / (dx * dx) : 0.0;
       di[off + p] = -2.0 * ga / (dx * dx) + mu;
@@ -73,10 +73,83 @@ rsv_status build_gl1d(rsv_operator op, const rsv_operator_desc* d) {
     }
   }
   const std::vector<std::complex<double>>* arrs[6] = {&lo, &di, &up, &alo, &adi, &aup};
+  op->tri_host.assign((size_t)12 * tot, 0.0);
   for (int a = 0; a < 6; ++a) {
     rsv_status s = upload_cvec(op, *arrs[a], &op->tri[a]);
     if (s != RSV_OK) return s;
+    for (int64_t p = 0; p < tot; ++p) {
+      op->tri_host[(size_t)2 * (a * tot + p)] = (*arrs[a])[p].real();
+      op->tri_host[(size_t)2 * (a * tot + p) + 1] = (*arrs[a])[p].imag();
+    }
   }
+  return RSV_OK;
+}
+
+// Cyclic-reduction factors of I - h/2 A (Crank-Nicolson), direct and adjoint, per instance, in FP64:
+// with b, a, c the diagonal and the couplings to i - s and i + s, level l (s = 2^l) eliminates
+// both neighbours, k1 = a_i / b_{i-s}, k2 = c_i / b_{i+s}; a_i <- -k1 a_{i-s}, c_i <- -k2 c_{i+s},
+// b_i <- b_i - k1 c_{i-s} - k2 a_{i+s}.  Stored: k1, k2 per level, then 1 / b after the last level.
+static rsv_status gl1d_cn_factors(rsv_operator op) {
+  using cdd = std::complex<double>;
+  const int64_t n = op->n;
+  int L = 0;
+  while ((1 << L) < op->gl_max_n) ++L;
+  const double hh = 0.5 * op->h;
+  std::vector<cdd> out((size_t)2 * (2 * L + 1) * n);
+  auto coef = [&](int a, int64_t p) {
+    return cdd(op->tri_host[(size_t)2 * (a * n + p)], op->tri_host[(size_t)2 * (a * n + p) + 1]);
+  };
+  for (int dir = 0; dir < 2; ++dir) {
+    cdd* K1 = out.data() + (size_t)dir * (2 * L + 1) * n;
+    cdd* K2 = K1 + (size_t)L * n;
+    cdd* INV = K2 + (size_t)L * n;
+    for (int i = 0; i < op->n_inst; ++i) {
+      const int64_t off = op->inst_off[i];
+      const int len = (int)op->inst_len[i];
+      std::vector<cdd> a(len), b(len), c(len), na(len), nb(len), nc(len);
+      for (int p = 0; p < len; ++p) {
+        b[p] = 1.0 - hh * coef(3 * dir + 1, off + p);
+        a[p] = p > 0 ? -hh * coef(3 * dir, off + p) : 0.0;
+        c[p] = p + 1 < len ? -hh * coef(3 * dir + 2, off + p) : 0.0;
+      }
+      for (int l = 0; l < L; ++l) {
+        const int sd = 1 << l;
+        for (int p = 0; p < len; ++p) {
+          const cdd k1 = p - sd >= 0 ? a[p] / b[p - sd] : 0.0;
+          const cdd k2 = p + sd < len ? c[p] / b[p + sd] : 0.0;
+          na[p] = p - sd >= 0 ? -k1 * a[p - sd] : 0.0;
+          nc[p] = p + sd < len ? -k2 * c[p + sd] : 0.0;
+          nb[p] = b[p] - (p - sd >= 0 ? k1 * c[p - sd] : 0.0) - (p + sd < len ? k2 * a[p + sd] : 0.0);
+          K1[(size_t)l * n + off + p] = k1;
+          K2[(size_t)l * n + off + p] = k2;
+        }
+        a.swap(na);
+        b.swap(nb);
+        c.swap(nc);
+      }
+      for (int p = 0; p < len; ++p) {
+        if (!(std::abs(b[p]) > 0.0)) return fail(RSV_ERR_INVALID_ARG, "Crank-Nicolson matrix is singular");
+        INV[off + p] = 1.0 / b[p];
+      }
+    }
+  }
+  if (op->pcr) cudaFree(op->pcr);
+  op->pcr = nullptr;
+  const size_t cnt = out.size();
+  cudaError_t e;
+  if (op->prec == RSV_PREC_FP64) {
+    std::vector<cpx<double>> o(cnt);
+    for (size_t i = 0; i < cnt; ++i) o[i] = mk<double>(out[i].real(), out[i].imag());
+    e = cudaMalloc(&op->pcr, cnt * sizeof(cpx<double>));
+    if (e == cudaSuccess) e = cudaMemcpy(op->pcr, o.data(), cnt * sizeof(cpx<double>), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<cpx<float>> o(cnt);
+    for (size_t i = 0; i < cnt; ++i) o[i] = mk<float>((float)out[i].real(), (float)out[i].imag());
+    e = cudaMalloc(&op->pcr, cnt * sizeof(cpx<float>));
+    if (e == cudaSuccess) e = cudaMemcpy(op->pcr, o.data(), cnt * sizeof(cpx<float>), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "Crank-Nicolson factors");
+  op->pcr_levels = L;
   return RSV_OK;
 }
 
@@ -117,6 +190,7 @@ int march_tile_kernels(rsv_operator op, int steps, int kg) {
 
 rsv_status on_frequencies(rsv_operator op) {
   if (op->kind == RSV_OP_DENSE) return dense_on_frequencies(op);
+  if (op->kind == RSV_OP_GL1D && op->scheme == RSV_SCHEME_CN) return gl1d_cn_factors(op);
   return RSV_OK;
 }
 
@@ -287,6 +361,17 @@ static Gl1dTile gl1d_geom(rsv_operator op, bool adjoint, int kg) {
   g.n_forced = 0;
   g.y_first = 0;
   g.real_state = false;
+  g.cr_lo = g.cr_up = g.cr_inv = nullptr;
+  g.cr_levels = 0;
+  if (op->scheme == RSV_SCHEME_CN && op->pcr) {
+    const size_t es = op->prec == RSV_PREC_FP64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+    const int L = op->pcr_levels;
+    const char* base = static_cast<const char*>(op->pcr) + (size_t)(adjoint ? 1 : 0) * (2 * L + 1) * op->n * es;
+    g.cr_lo = base;
+    g.cr_up = base + (size_t)L * op->n * es;
+    g.cr_inv = base + (size_t)2 * L * op->n * es;
+    g.cr_levels = L;                // >= 1: every instance has at least two points
+  }
   return g;
 }
 

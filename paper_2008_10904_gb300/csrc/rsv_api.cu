@@ -124,6 +124,7 @@ rsv_operator_s::~rsv_operator_s() {
   if (d_cw) cudaFree(d_cw);
   if (d_flag) cudaFree(d_flag);
   if (d_wt) cudaFree(d_wt);
+  if (pcr) cudaFree(pcr);
   if (ws_scaled.ptr) cudaFree(ws_scaled.ptr);
   for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
 }
@@ -165,8 +166,12 @@ extern "C" rsv_status rsv_create_operator(const rsv_operator_desc* d, void* stre
   if (d->precision != RSV_PREC_FP64 && d->precision != RSV_PREC_FP32)
     return fail(RSV_ERR_INVALID_ARG, "unknown precision");
   if (!(d->dt > 0.0)) return fail(RSV_ERR_INVALID_ARG, "dt must be positive");
+  if (d->scheme != RSV_SCHEME_RK4 && d->scheme != RSV_SCHEME_CN) return fail(RSV_ERR_INVALID_ARG, "unknown scheme");
+  if (d->scheme == RSV_SCHEME_CN && d->kind != RSV_OP_GL1D)
+    return fail(RSV_ERR_INVALID_ARG, "the Crank-Nicolson scheme is built for the GL1D kind only");
   rsv_operator op = new rsv_operator_s();
   op->kind = d->kind;
+  op->scheme = d->scheme;
   op->prec = d->precision;
   op->dt = d->dt;
   op->stream = (cudaStream_t)stream;
@@ -177,6 +182,16 @@ extern "C" rsv_status rsv_create_operator(const rsv_operator_desc* d, void* stre
     // RSV_CONTRACT_TENSOR=0 keeps FP32 synthesis / analysis on the CUDA cores (for comparisons)
     const char* env2 = getenv("RSV_CONTRACT_TENSOR");
     op->tc_contract_disabled = env2 != nullptr && env2[0] == '0';
+    // RSV_WAIT_LIMIT_NS shortens the limit of the persistent kernels' waits on other CTAs; with
+    // RSV_TEST_STALL_WAIT=1 the dense persistent kernel's first wait targets a count nobody
+    // reaches, so a test can make a bounded wait run out and check RSV_ERR_TIMEOUT
+    const char* env3 = getenv("RSV_WAIT_LIMIT_NS");
+    if (env3 != nullptr) {
+      const long long v = atoll(env3);
+      if (v > 0) op->wait_limit_ns = (uint64_t)v;
+    }
+    const char* env4 = getenv("RSV_TEST_STALL_WAIT");
+    op->test_stall_wait = env4 != nullptr && env4[0] == '1';
   }
   int dev = 0;
   cudaGetDevice(&dev);
@@ -223,7 +238,12 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
   if (!op || !buf || buflen < 1) return fail(RSV_ERR_INVALID_ARG, "bad describe arguments");
   static const char* kinds[] = {"gl1d", "dense", "adr2d", "adv3d"};
   const char* path = "cuda-core stages";
-  if (op->kind == RSV_OP_GL1D) path = "cuda-core tile kernel";
+  if (op->kind == RSV_OP_GL1D)
+    path = op->scheme == RSV_SCHEME_CN ? "cuda-core crank-nicolson tile kernel" : "cuda-core tile kernel";
+  if (op->kind == RSV_OP_ADV3D && op->prec == RSV_PREC_FP32) {
+    const char* e = getenv("RSV_STENCIL3D_STAGED");
+    path = (e != nullptr && e[0] == '1') ? "cuda-core stages" : "cuda-core 3-D stage-pair kernels";
+  }
   if (op->kind == RSV_OP_ADR2D) {
     const char* e = getenv("RSV_STENCIL_FUSED");
     if (e != nullptr && e[0] == '1') path = "cuda-core whole-step kernel";

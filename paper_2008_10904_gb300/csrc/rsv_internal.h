@@ -118,6 +118,13 @@ struct rsv_operator_s {
   // GL1D: tridiagonal coefficients, direct then adjoint: lo, di, up
   void* tri[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int gl_max_n = 0;
+  // Crank-Nicolson (scheme = RSV_SCHEME_CN): host copies of the tridiagonal coefficients (FP64,
+  // direct then adjoint: lo, di, up) and, per step h, the cyclic-reduction factors of
+  // I - h/2 A on the device: [dir][level][n] for both neighbours, then [dir][n] inverse pivots
+  int scheme = RSV_SCHEME_RK4;
+  std::vector<double> tri_host;           // [6][n] complex (re, im)
+  void* pcr = nullptr;
+  int pcr_levels = 0;
   // DENSE: A (FP64), A and A^H in the element type, and the RK4 propagator
   // blocks D, P1, P2, D^H, P1^H, P2^H (element type) for the step dense_h
   void* dense64[1] = {nullptr};
@@ -128,6 +135,8 @@ struct rsv_operator_s {
   void* tc_tiles[2] = {nullptr, nullptr};
   bool tc_disabled = false;
   bool tc_persistent = false;   // all clusters of the tile kernel fit on the GPU at once
+  uint64_t wait_limit_ns = 2000000000ull;  // limit of each cross-CTA wait (RSV_WAIT_LIMIT_NS)
+  bool test_stall_wait = false;  // test hook (RSV_TEST_STALL_WAIT=1): a wait on a count nobody reaches
   int tc_max_clusters = 0;      // resident CTAs of the persistent tile kernel on this GPU
   void* d_ready = nullptr;      // per-block step counters and arrival counters of the persistent tile kernel
   void* tc_acc = nullptr;       // its FP32 partial-sum accumulators
@@ -231,6 +240,11 @@ struct Gl1dTile {
   const void* lo;
   const void* di;
   const void* up;
+  // Crank-Nicolson: cyclic-reduction factors of I - h/2 A ([levels][n] each) and inverse pivots [n]
+  const void* cr_lo;
+  const void* cr_up;
+  const void* cr_inv;
+  int cr_levels;
   const int64_t* inst_off;  // [n_inst + 1]
   int n_inst, max_n;
   int64_t n;                // points per vector

@@ -581,6 +581,8 @@ constexpr int k3UW = k3TX + 4, k3UH = k3TY + 4;     // ring of the pair's stenci
 constexpr int k3XW = k3TX + 2, k3XH = k3TY + 2;     // ring of the intermediate stage (halo 1)
 constexpr int k3UP = k3UW * k3UH, k3XP = k3XW * k3XH;
 constexpr int k3Threads = 256;
+constexpr int k3S1 = (k3XP + k3Threads - 1) / k3Threads;   // first-stage cells per thread (3)
+constexpr int k3S2 = k3TX * k3TY / k3Threads;              // second-stage cells per thread (2)
 constexpr size_t k3Smem = sizeof(float) * (4 * 3 * (size_t)k3UP + 3 * 3 * (size_t)k3XP);
 
 struct Pair3D {
@@ -595,54 +597,77 @@ struct Pair3D {
   float h;
 };
 
-// 7-point operator (forward or transposed) of component-interleaved planes at local (lx, ly) of a
-// plane with width W, for the cell (i, j, kz) of the grid; x planes: below, centre, above.
+// Base flow at one cell, as the operator's fields hold it (U = erf(r / delta(x)) and its gradient):
+// forward advection uses U at the cell, the transposed advection U at the two x neighbours.
+struct Bf {
+  float Uc, Uw, Ue, Ux, Uy, Uz;
+};
+
+// 7-point operator (forward or transposed) of component-interleaved shared-memory planes at local
+// (lx, ly) of a plane of width W; planes below, centre, above.
 template <bool ADJ, int W, int PLANE>
 __device__ __forceinline__ void op3d_smem(const float* __restrict__ xb, const float* __restrict__ xc,
-                                          const float* __restrict__ xt, int lx, int ly, int i, int64_t q,
-                                          const StGeom& g, float cdx, float idx2, float idy2, float idz2,
-                                          float nu, float out[3]) {
-  const float* U = reinterpret_cast<const float*>(g.f0);
-  const float* Ux = reinterpret_cast<const float*>(g.f1);
-  const float* Uy = reinterpret_cast<const float*>(g.f2);
-  const float* Uz = reinterpret_cast<const float*>(g.f3);
+                                          const float* __restrict__ xt, int lx, int ly, const Bf& bf, float cdx,
+                                          float idx2, float idy2, float idz2, float nu, float out[3]) {
   const int e = ly * W + lx;
   float xcen[3];
-  float uw = 0.f, ue = 0.f, uc = 0.f;
-  if (ADJ) {
-    uw = i > 0 ? __ldg(U + q - 1) : 0.f;
-    ue = i < g.nx - 1 ? __ldg(U + q + 1) : 0.f;
-  } else {
-    uc = __ldg(U + q);
-  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float* pc = xc + c * PLANE;
     const float cc = pc[e], w = pc[e - 1], ee = pc[e + 1], s = pc[e - W], n = pc[e + W];
     const float b = xb[c * PLANE + e], t = xt[c * PLANE + e];
     xcen[c] = cc;
-    const float adv = ADJ ? (ue * ee - uw * w) * cdx : -uc * (ee - w) * cdx;
+    const float adv = ADJ ? (bf.Ue * ee - bf.Uw * w) * cdx : -bf.Uc * (ee - w) * cdx;
     out[c] = adv + nu * (idx2 * (w + ee - 2.f * cc) + idy2 * (s + n - 2.f * cc) + idz2 * (b + t - 2.f * cc));
   }
-  const float gx = __ldg(Ux + q), gy = __ldg(Uy + q), gz = __ldg(Uz + q);
   if (ADJ) {
-    out[0] -= gx * xcen[0];
-    out[1] -= gy * xcen[0];
-    out[2] -= gz * xcen[0];
+    out[0] -= bf.Ux * xcen[0];
+    out[1] -= bf.Uy * xcen[0];
+    out[2] -= bf.Uz * xcen[0];
   } else {
-    out[0] -= gx * xcen[0] + gy * xcen[1] + gz * xcen[2];
+    out[0] -= bf.Ux * xcen[0] + bf.Uy * xcen[1] + bf.Uz * xcen[2];
   }
 }
 
-template <bool ADJ, bool PAIR_B>
-__global__ void __launch_bounds__(k3Threads) adv3d_pair_kernel(StGeom g, Pair3D P) {
+// Base-flow fields at grid cell q (i its x index), for the forward or transposed operator.
+template <bool ADJ>
+__device__ __forceinline__ Bf load_bf(const StGeom& g, int64_t q, int i, bool ok) {
+  const float* U = reinterpret_cast<const float*>(g.f0);
+  const float* Ux = reinterpret_cast<const float*>(g.f1);
+  const float* Uy = reinterpret_cast<const float*>(g.f2);
+  const float* Uz = reinterpret_cast<const float*>(g.f3);
+  Bf b;
+  b.Uc = (!ADJ && ok) ? __ldg(U + q) : 0.f;
+  b.Uw = (ADJ && ok && i > 0) ? __ldg(U + q - 1) : 0.f;
+  b.Ue = (ADJ && ok && i < g.nx - 1) ? __ldg(U + q + 1) : 0.f;
+  b.Ux = ok ? __ldg(Ux + q) : 0.f;
+  b.Uy = ok ? __ldg(Uy + q) : 0.f;
+  b.Uz = ok ? __ldg(Uz + q) : 0.f;
+  return b;
+}
+
+// Per-thread registers of one plane's point inputs, loaded one plane ahead of their use.
+struct Stage1In {
+  float f[k3S1][3];    // forcing of the first stage
+  float u[k3S1][3];    // pair B: the state u
+  Bf bf[k3S1];         // base flow
+};
+struct Stage2In {
+  float f[k3S2][3];    // forcing of the second stage
+  float u[k3S2][3];    // pair B: the state u
+  float a[k3S2][3];    // pair B: the accumulator
+  Bf bf[k3S2];         // base flow
+};
+
+template <bool ADJ, bool PAIR_B, int MINB>
+__global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, Pair3D P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);            // [4 planes][3 comps][k3UP]
   float* mid = ring + 4 * 3 * k3UP;                              // [3 planes][3 comps][k3XP]
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int64_t ncell = (int64_t)nx * ny * nz;
   const int64_t plane = (int64_t)nx * ny;
-  // block order: vector fastest (base-flow fields of a tile shared through L2), then x, y, z
+  // block order: vector fastest (neighbouring tiles of all vectors in flight together), then x, y, z
   int b = blockIdx.x;
   const int v = b % g.kg;
   b /= g.kg;
@@ -653,14 +678,17 @@ __global__ void __launch_bounds__(k3Threads) adv3d_pair_kernel(StGeom g, Pair3D 
   const int z0 = (b / nty) * k3ZC;
   const int z1 = min(z0 + k3ZC, nz);
   const int64_t base = (int64_t)v * g.n;
-  const float* in = P.in + base;
+  const float* __restrict__ in = P.in + base;
+  const float* __restrict__ fa = P.fa;
+  const float* __restrict__ fb = P.fb;
+  const float* __restrict__ pu = P.u;
+  const float* __restrict__ pacc = P.acc;
   const float cdx = 0.5f / (float)g.dx, idx2 = 1.f / ((float)g.dx * (float)g.dx);
   const float idy2 = 1.f / ((float)g.dy * (float)g.dy), idz2 = 1.f / ((float)g.dz * (float)g.dz);
   const float nu = (float)g.visc;
   const float h = P.h;
-  // stage coefficients: pair A x2 = u + h/2 k1; pair B x4 = u + h k3
-  const float c1 = PAIR_B ? h : 0.5f * h;
-  const float c2 = PAIR_B ? h / 6.f : 0.5f * h;     // pair A: x3 = u + h/2 k2; pair B: u' = ... + h/6 k4
+  const float c1 = PAIR_B ? h : 0.5f * h;       // x_mid = u + c1 (A x + f_a)
+  const float c2 = PAIR_B ? h / 6.f : 0.5f * h;  // pair A: x3 = u + h/2 k2; pair B: u' = ... + h/6 k4
   const int tid = threadIdx.x;
 
   // asynchronous copy of plane kz of the stencil input (tile + 2 halo cells) into ring slot kz & 3
@@ -677,29 +705,64 @@ __global__ void __launch_bounds__(k3Threads) adv3d_pair_kernel(StGeom g, Pair3D 
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
+  // point inputs of the first stage on plane kz (tile + 1 halo), into registers
+  auto fetch1 = [&](int kz, Stage1In& r) {
+#pragma unroll
+    for (int sl = 0; sl < k3S1; ++sl) {
+      const int e = tid + sl * k3Threads;
+      const int gi = X0 - 1 + e % k3XW, gj = Y0 - 1 + e / k3XW;
+      const bool ok = e < k3XP && kz >= 0 && kz < nz && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+      const int64_t qc = (int64_t)kz * plane + (int64_t)gj * nx + gi;
+      const int64_t q = base + qc;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        r.f[sl][c] = (ok && fa) ? __ldg(fa + q + c * ncell) : 0.f;
+        r.u[sl][c] = (PAIR_B && ok) ? __ldg(pu + q + c * ncell) : 0.f;
+      }
+      r.bf[sl] = load_bf<ADJ>(g, qc, gi, ok);
+    }
+  };
+  // point inputs of the second stage on plane kz (the tile), into registers
+  auto fetch2 = [&](int kz, Stage2In& r) {
+#pragma unroll
+    for (int sl = 0; sl < k3S2; ++sl) {
+      const int e = tid + sl * k3Threads;
+      const int gi = X0 + e % k3TX, gj = Y0 + e / k3TX;
+      const bool ok = kz >= z0 && kz < z1 && gi < nx && gj < ny;
+      const int64_t qc = (int64_t)kz * plane + (int64_t)gj * nx + gi;
+      const int64_t q = base + qc;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        r.f[sl][c] = (ok && fb) ? __ldg(fb + q + c * ncell) : 0.f;
+        r.u[sl][c] = (PAIR_B && ok) ? __ldg(pu + q + c * ncell) : 0.f;
+        r.a[sl][c] = (PAIR_B && ok) ? __ldg(pacc + q + c * ncell) : 0.f;
+      }
+      r.bf[sl] = load_bf<ADJ>(g, qc, gi, ok);
+    }
+  };
 
-  // first stage of the pair on plane kz, tile + 1 halo cell: x_mid = u + c1 (A x + f_a); zero outside the grid
-  auto first_stage = [&](int kz) {
-    float* dst = mid + (size_t)(kz % 3 + 3) % 3 * 3 * k3XP;
+  // first stage on plane kz, tile + 1 halo cell: x_mid = u + c1 (A x + f_a); zero outside the grid
+  auto first_stage = [&](int kz, const Stage1In& r) {
+    float* dst = mid + (size_t)(((kz % 3) + 3) % 3) * 3 * k3XP;
     const float* xb = ring + (size_t)((kz - 1) & 3) * 3 * k3UP;
     const float* xc = ring + (size_t)(kz & 3) * 3 * k3UP;
     const float* xt = ring + (size_t)((kz + 1) & 3) * 3 * k3UP;
     const bool zin = kz >= 0 && kz < nz;
-    for (int e = tid; e < k3XP; e += k3Threads) {
+#pragma unroll
+    for (int sl = 0; sl < k3S1; ++sl) {
+      const int e = tid + sl * k3Threads;
+      if (e >= k3XP) break;
       const int lx = e % k3XW, ly = e / k3XW;
       const int gi = X0 - 1 + lx, gj = Y0 - 1 + ly;
       float xo[3] = {0.f, 0.f, 0.f};
       if (zin && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
-        const int64_t q = (int64_t)kz * plane + (int64_t)gj * nx + gi;
         float k[3];
-        op3d_smem<ADJ, k3UW, k3UP>(xb, xc, xt, lx + 1, ly + 1, gi, q, g, cdx, idx2, idy2, idz2, nu, k);
+        op3d_smem<ADJ, k3UW, k3UP>(xb, xc, xt, lx + 1, ly + 1, r.bf[sl], cdx, idx2, idy2, idz2, nu, k);
         const int eu = (ly + 1) * k3UW + lx + 1;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const int64_t pidx = base + c * ncell + q;
-          const float fv = P.fa ? __ldg(P.fa + pidx) : 0.f;
-          const float uu = PAIR_B ? __ldg(P.u + pidx) : xc[c * k3UP + eu];
-          xo[c] = uu + c1 * (k[c] + fv);
+          const float uu = PAIR_B ? r.u[sl][c] : xc[c * k3UP + eu];
+          xo[c] = uu + c1 * (k[c] + r.f[sl][c]);
         }
       }
 #pragma unroll
@@ -707,74 +770,98 @@ __global__ void __launch_bounds__(k3Threads) adv3d_pair_kernel(StGeom g, Pair3D 
     }
   };
 
-  // second stage of the pair on plane kz, the tile
-  auto second_stage = [&](int kz) {
-    const float* mb = mid + (size_t)((kz - 1) % 3 + 3) % 3 * 3 * k3XP;
+  // second stage on plane kz, the tile
+  auto second_stage = [&](int kz, const Stage2In& r) {
+    const float* mb = mid + (size_t)((((kz - 1) % 3) + 3) % 3) * 3 * k3XP;
     const float* mc = mid + (size_t)(kz % 3) * 3 * k3XP;
     const float* mt = mid + (size_t)((kz + 1) % 3) * 3 * k3XP;
     const float* uc = ring + (size_t)(kz & 3) * 3 * k3UP;
-    for (int e = tid; e < k3TX * k3TY; e += k3Threads) {
+#pragma unroll
+    for (int sl = 0; sl < k3S2; ++sl) {
+      const int e = tid + sl * k3Threads;
       const int tx = e % k3TX, ty = e / k3TX;
       const int gi = X0 + tx, gj = Y0 + ty;
       if (gi >= nx || gj >= ny) continue;
       const int64_t q = (int64_t)kz * plane + (int64_t)gj * nx + gi;
       float k[3];
-      op3d_smem<ADJ, k3XW, k3XP>(mb, mc, mt, tx + 1, ty + 1, gi, q, g, cdx, idx2, idy2, idz2, nu, k);
+      op3d_smem<ADJ, k3XW, k3XP>(mb, mc, mt, tx + 1, ty + 1, r.bf[sl], cdx, idx2, idy2, idz2, nu, k);
       const int em = (ty + 1) * k3XW + tx + 1;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const int64_t pidx = base + c * ncell + q;
-        const float fv = P.fb ? __ldg(P.fb + pidx) : 0.f;
         const float xm = mc[c * k3XP + em];
         if (!PAIR_B) {
           const float uu = uc[c * k3UP + (ty + 2) * k3UW + tx + 2];
-          const float kk = k[c] + fv;
-          P.out[pidx] = uu + c2 * kk;                                      // x3
-          P.acc_out[pidx] = uu + (xm - uu) * (1.f / 3.f) + (h / 3.f) * kk;  // u + h/6 k1 + h/3 k2
+          const float kk = k[c] + r.f[sl][c];
+          P.out[pidx] = uu + c2 * kk;                                       // x3
+          P.acc_out[pidx] = uu + (xm - uu) * (1.f / 3.f) + (h / 3.f) * kk;   // u + h/6 k1 + h/3 k2
           if (P.ysnap) P.ysnap[pidx] = uu;
         } else {
-          const float uu = __ldg(P.u + pidx);
-          const float a = __ldg(P.acc + pidx) + (xm - uu) * (1.f / 3.f);   // + h/3 k3
-          P.out[pidx] = a + c2 * (k[c] + fv);                              // + h/6 k4
+          const float uu = r.u[sl][c];
+          const float a = r.a[sl][c] + (xm - uu) * (1.f / 3.f);             // + h/3 k3
+          P.out[pidx] = a + c2 * (k[c] + r.f[sl][c]);                       // + h/6 k4
         }
       }
     }
   };
 
-  // prologue: planes z0 - 2 .. z0 + 1 of the stencil input, first stage on plane z0 - 1
+  Stage1In s1;
+  Stage2In s2;
+  // prologue: planes z0 - 2 .. z0 + 1 of the stencil input; first stage on plane z0 - 1
   for (int kz = z0 - 2; kz <= z0 + 1; ++kz) load_plane(kz);
+  fetch1(z0 - 1, s1);
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  first_stage(z0 - 1);
+  first_stage(z0 - 1, s1);
+  fetch1(z0, s1);
+  fetch2(z0, s2);
   for (int p = z0 - 1; p < z1; ++p) {
-    // plane p + 2 has landed (the prologue or the previous iteration's copy); the slot of
-    // plane p - 1 is free: it receives plane p + 3 while this iteration computes
+    // plane p + 2 has landed; the slot of plane p - 1 is free and receives plane p + 3
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     if (p + 3 <= z1 + 1) load_plane(p + 3);
-    first_stage(p + 1);
+    first_stage(p + 1, s1);
+    if (p + 2 <= z1) fetch1(p + 2, s1);         // in flight during the barrier and the second stage
     __syncthreads();
-    if (p >= z0) second_stage(p);
+    if (p >= z0) {
+      second_stage(p, s2);
+      if (p + 1 < z1) fetch2(p + 1, s2);
+    }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-template <bool ADJ, bool PAIR_B>
-cudaError_t launch_pair3d(rsv_operator op, const StGeom& g, const Pair3D& P) {
+// Resident CTAs per SM the pair kernels are compiled for: 2 (no spills, the default) or 3 (80
+// registers, spills); RSV_PAIR3D_MINB selects (read once per process).
+int pair3d_minb() {
+  static int v = [] {
+    const char* e = getenv("RSV_PAIR3D_MINB");
+    return (e != nullptr && e[0] == '3') ? 3 : 2;
+  }();
+  return v;
+}
+
+template <bool ADJ, bool PAIR_B, int MINB>
+cudaError_t launch_pair3d_minb(rsv_operator op, const StGeom& g, const Pair3D& P) {
   static int attr_dev[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_dev[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(adv3d_pair_kernel<ADJ, PAIR_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)k3Smem);
+    cudaError_t e = cudaFuncSetAttribute(adv3d_pair_kernel<ADJ, PAIR_B, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3Smem);
     if (e != cudaSuccess) return e;
     attr_dev[dev] = 1;
   }
   const unsigned ntx = (unsigned)((g.nx + k3TX - 1) / k3TX), nty = (unsigned)((g.ny + k3TY - 1) / k3TY);
   const unsigned ntz = (unsigned)((g.nz + k3ZC - 1) / k3ZC);
   const unsigned blocks = ntx * nty * ntz * (unsigned)g.kg;
-  adv3d_pair_kernel<ADJ, PAIR_B><<<blocks, k3Threads, k3Smem, op->stream>>>(g, P);
+  adv3d_pair_kernel<ADJ, PAIR_B, MINB><<<blocks, k3Threads, k3Smem, op->stream>>>(g, P);
   return cudaGetLastError();
+}
+
+template <bool ADJ, bool PAIR_B>
+cudaError_t launch_pair3d(rsv_operator op, const StGeom& g, const Pair3D& P) {
+  return pair3d_minb() == 2 ? launch_pair3d_minb<ADJ, PAIR_B, 2>(op, g, P) : launch_pair3d_minb<ADJ, PAIR_B, 3>(op, g, P);
 }
 
 // RSV_STENCIL3D_STAGED=1 keeps FP32 3-D marches on the four single-stage kernels (comparisons).

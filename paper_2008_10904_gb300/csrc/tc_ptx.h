@@ -36,14 +36,17 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Upper bound of any single wait: 2 seconds of wall time.
+// Default upper bound of any single wait: 2 seconds of wall time.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 // Wait for the phase with the given parity to complete; false after `max_tries`
-// polls or kWaitLimitNs, whichever comes first, or (when `abort_flag` is given)
-// once *abort_flag is non-zero.
+// polls or limit_ns, whichever comes first, or (when `abort_flag` is given)
+// once *abort_flag is non-zero.  Waits for copies or MMAs this CTA issued pass no
+// abort flag: they end when the hardware completes them (or the limit passes), so a
+// CTA never leaves with its own asynchronous work in flight.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_tries,
-                                          const volatile int* abort_flag = nullptr) {
+                                          const volatile int* abort_flag = nullptr,
+                                          uint64_t limit_ns = kWaitLimitNs) {
   const uint32_t a = smem_u32(bar);
   uint64_t t0 = 0;
   for (uint32_t i = 0; i < max_tries; ++i) {
@@ -60,7 +63,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
       if (abort_flag != nullptr && *abort_flag) return false;
       const uint64_t now = global_ns();
       if (t0 == 0) t0 = now;
-      else if (now - t0 > kWaitLimitNs) return false;
+      else if (now - t0 > limit_ns) return false;
     }
   }
   return false;
@@ -209,8 +212,9 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
   asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Spin (one thread) until *p >= target, bounded by kWaitLimitNs; also stops once *err != 0.
-__device__ __forceinline__ bool spin_until_geq(const int* p, int target, const volatile int* err) {
+// Spin (one thread) until *p >= target, bounded by limit_ns; also stops once *err != 0.
+__device__ __forceinline__ bool spin_until_geq(const int* p, int target, const volatile int* err,
+                                               uint64_t limit_ns = kWaitLimitNs) {
   uint64_t t0 = 0;
   for (uint32_t i = 0;; ++i) {
     if (ld_acquire(p) >= target) return true;
@@ -218,7 +222,7 @@ __device__ __forceinline__ bool spin_until_geq(const int* p, int target, const v
       if (*err != 0) return false;
       const uint64_t now = global_ns();
       if (t0 == 0) t0 = now;
-      else if (now - t0 > kWaitLimitNs) return false;
+      else if (now - t0 > limit_ns) return false;
     }
   }
 }

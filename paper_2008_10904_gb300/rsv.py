@@ -22,6 +22,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "NOT_COMMENSURATE", 4: "D
 RSV_OP_GL1D, RSV_OP_DENSE, RSV_OP_ADR2D, RSV_OP_ADV3D = 0, 1, 2, 3
 RSV_PREC_FP64, RSV_PREC_FP32 = 0, 1
 RSV_SSRM, RSV_TRM = 0, 1
+RSV_SCHEME_RK4, RSV_SCHEME_CN = 0, 1
 
 
 class RsvError(RuntimeError):
@@ -43,6 +44,7 @@ class rsv_operator_desc(ctypes.Structure):
         ("visc", ctypes.c_double), ("kappa", ctypes.c_double), ("jet_delta", ctypes.c_double),
         ("sponge_amp", ctypes.c_double), ("sponge_cells", ctypes.c_int32),
         ("delta0", ctypes.c_double), ("delta1", ctypes.c_double),
+        ("mu1", ctypes.c_double), ("scheme", ctypes.c_int32),
     ]
 
 
@@ -311,7 +313,7 @@ def rsv_version() -> str:
 # ---------------------------------------------------------------------------
 # Descriptor marshalling from the workload parameter objects
 # ---------------------------------------------------------------------------
-def desc_for(system, dt: float, precision: int):
+def desc_for(system, dt: float, precision: int, scheme: int = RSV_SCHEME_RK4):
     """rsv_operator_desc for a workloads.GL1D / Dense / ADR2D / ADV3D object.
 
     Returns (desc, keep) where `keep` holds the host arrays the descriptor
@@ -320,6 +322,7 @@ def desc_for(system, dt: float, precision: int):
     d = rsv_operator_desc()
     d.precision = precision
     d.dt = float(dt)
+    d.scheme = int(scheme)
     keep = []
     name = type(system).__name__
     if name == "GL1D":
@@ -334,6 +337,7 @@ def desc_for(system, dt: float, precision: int):
         d.nu_re, d.nu_im = system.nu.real, system.nu.imag
         d.gamma_re, d.gamma_im = system.gamma.real, system.gamma.imag
         d.mu_shift, d.mu2 = system.mu_shift, system.mu2
+        d.mu1 = getattr(system, "mu1", 0.0)
     elif name == "Dense":
         raise ValueError("a dense system needs its matrix: use desc_dense")
     elif name == "ADR2D":
@@ -363,12 +367,13 @@ def desc_dense(a: np.ndarray, dt: float, precision: int):
     return d, [a]
 
 
-def create_for_workload(w, precision: int, stream=None, dense_matrix=None) -> Operator:
+def create_for_workload(w, precision: int, stream=None, dense_matrix=None, scheme: int = RSV_SCHEME_RK4) -> Operator:
     """Create an operator for a workloads.Workload and set its frequencies."""
     if type(w.system).__name__ == "Dense":
         d, keep = desc_dense(dense_matrix, w.dt, precision)
+        d.scheme = int(scheme)
     else:
-        d, keep = desc_for(w.system, w.dt, precision)
+        d, keep = desc_for(w.system, w.dt, precision, scheme)
     op = rsv_create_operator(d, stream, keep)
     rsv_set_frequencies(op, w.omegas)
     return op

@@ -188,3 +188,41 @@ def test_dense_fp32_size_outside_tensor_tiles(rsv):
         assert rel_rows(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh)) < TOL32_MARCH
     finally:
         rsv.rsv_destroy_operator(op)
+
+
+def test_bounded_wait_runs_out(rsv, monkeypatch):
+    """Failure detection without a GPU fault: with the test hook RSV_TEST_STALL_WAIT=1 the dense
+    persistent kernel's first wait targets a step count that nothing reaches; with the limit
+    RSV_WAIT_LIMIT_NS = 200 us the wait gives up, the kernel finishes every step without issuing
+    copies or products, frees its tensor memory and returns, and the march reports RSV_ERR_TIMEOUT.
+    An operator created afterwards marches correctly (the context stays usable)."""
+    import time
+    import torch
+    sysm = W.Dense(n=128, x_half_width=30.0)
+    w = W.Workload("dense_stall", sysm, np.linspace(-1.0, 1.0, 8), 0.01, 5, "trm", tail_steps=300)
+    a = W.hermite_gl_matrix(sysm)
+    fh = W.test_block(w).astype(np.complex64).astype(np.complex128)
+    monkeypatch.setenv("RSV_TEST_STALL_WAIT", "1")
+    monkeypatch.setenv("RSV_WAIT_LIMIT_NS", "200000")
+    op = rsv.create_for_workload(w, 1, dense_matrix=a)
+    try:
+        assert "tcgen05 3xTF32 persistent" in rsv.rsv_describe(op)
+        x = _dev(fh, 1)
+        y = torch.empty_like(x)
+        t0 = time.perf_counter()
+        with pytest.raises(rsv.RsvError) as e:
+            rsv.rsv_march_direct(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=256))
+        assert e.value.status == 5, e.value
+        assert time.perf_counter() - t0 < 20.0
+    finally:
+        rsv.rsv_destroy_operator(op)
+    monkeypatch.delenv("RSV_TEST_STALL_WAIT")
+    monkeypatch.delenv("RSV_WAIT_LIMIT_NS")
+    op = rsv.create_for_workload(w, 1, dense_matrix=a)
+    try:
+        x = _dev(fh, 1)
+        y = torch.empty_like(x)
+        rsv.rsv_march_direct(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=256))
+        assert rel_rows(y.cpu().numpy().astype(np.complex128), _oracle(w, a, fh)) < TOL32_MARCH
+    finally:
+        rsv.rsv_destroy_operator(op)

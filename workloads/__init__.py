@@ -31,7 +31,7 @@ SEED_BASE = 2008109040
 class GL1D:
     """Linearised complex Ginzburg-Landau, du/dt = -nu u_x + gamma u_xx + mu(x) u.
 
-    mu(x) = mu0 + mu_shift + mu2 * x**2 on x in (x0, x1), n interior points
+    mu(x) = mu0 + mu_shift + mu1 * x + mu2 * x**2 on x in (x0, x1), n interior points
     per instance, homogeneous Dirichlet ends, 2nd-order central differences
     (Sec. 3, Eq. (GL_timeDomain) gives the model family).  A batch of instances with
     their own n and mu0 forms one block-diagonal operator.
@@ -44,6 +44,7 @@ class GL1D:
     gamma: complex = 1.0 - 1.0j
     mu_shift: float = -0.04
     mu2: float = -0.005
+    mu1: float = 0.0
 
     @property
     def n_total(self) -> int:
@@ -198,6 +199,19 @@ def gl_batch_c5(seed: int = SEED_BASE + 5) -> Workload:
     sysm = GL1D(n=tuple(int(v) for v in n), mu0=tuple(float(v) for v in mu0))
     return Workload("gl_batch64_k8_w64_ssrm", sysm, _lin(-1.5, 1.5, 64), 0.003, 8, "ssrm",
                     n_transient_windows=2, n_power_iter=4, seed=seed)
+
+
+def gl_paper(n: int = 400, beta: float = 0.1, n_omega: int = 61, dt: float = 0.01) -> Workload:
+    """The paper's Ginzburg-Landau validation case (Sec. 3): advection speed U = 6, gamma = 1 (real),
+    mu(x) = beta mu_c (1 - x/20) with mu_c = U^2 Re(gamma) / |gamma|^2 = 36, x in (0, 40), Dirichlet,
+    Crank-Nicolson with dt = 0.01, frequencies up to 15.  The paper's operator A_p = U d/dx - mu - gamma
+    d^2/dx^2 is -A here.  The paper gives no grid size: n = 400 interior points (dx = 40/401); the
+    frequency grid is 0, 0.25, ..., 15 for the steady-state method."""
+    mu_c = 36.0
+    sysm = GL1D(n=(n,), mu0=(beta * mu_c,), x0=0.0, x1=40.0, nu=6.0 + 0.0j, gamma=1.0 + 0.0j, mu_shift=0.0,
+                mu2=0.0, mu1=-beta * mu_c / 20.0)
+    return Workload(f"gl_paper_n{n}_cn", sysm, _lin(0.0, 15.0, n_omega), dt, 4, "ssrm", n_transient_windows=2,
+                    n_power_iter=2, seed=SEED_BASE + 7)
 
 
 def small_gl(n: int = 24, n_omega: int = 8, k: int = 2, dt: float = 0.05, x_half: float = 20.0,
