@@ -415,7 +415,8 @@ def accuracy_record(w, prec_name, dense, stream, rank):
     opts = rsv.march_opts_for(ws)
     t0 = time.perf_counter()
     res = {}
-    for prec, cdt in ((rsv.RSV_PREC_FP32, torch.complex64), (rsv.RSV_PREC_FP64, torch.complex128)):
+    low = rsv.RSV_PREC_BF16_STATE if prec_name == "bf16" else rsv.RSV_PREC_FP32
+    for prec, cdt in ((low, torch.complex64), (rsv.RSV_PREC_FP64, torch.complex128)):
         op = rsv.create_for_workload(ws, prec, stream=stream.cuda_stream, dense_matrix=dense)
         gains = np.zeros((ninst, ws.n_omega, nm))
         modes = torch.empty((ws.n_omega, nm, ws.n), dtype=cdt, device="cuda")
@@ -426,7 +427,7 @@ def accuracy_record(w, prec_name, dense, stream, rank):
         del modes
     del x
     torch.cuda.empty_cache()
-    g32, m32 = res[rsv.RSV_PREC_FP32]
+    g32, m32 = res[low]
     g64, m64 = res[rsv.RSV_PREC_FP64]
     return {"gain_rel_err_max": float(np.max(np.abs(g32 - g64) / np.abs(g64))),
             "subspace_angle_max_rad": subspace_angle_max(m32, m64, segs),
@@ -491,7 +492,7 @@ def run_ours(args):
     name = args.workload
     w = workload(name)
     prec_name = args.precision or default_precision(name)
-    prec = rsv.RSV_PREC_FP64 if prec_name == "fp64" else rsv.RSV_PREC_FP32
+    prec = {"fp64": rsv.RSV_PREC_FP64, "fp32": rsv.RSV_PREC_FP32, "bf16": rsv.RSV_PREC_BF16_STATE}[prec_name]
     cdt = torch.complex128 if prec_name == "fp64" else torch.complex64
     dense = W.hermite_gl_matrix(w.system) if type(w.system).__name__ == "Dense" else None
     stream = torch.cuda.current_stream()
@@ -588,7 +589,8 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": "actions/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec_name == "fp64" else "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "f32 (bf16 state storage)"}[prec_name],
         "data": "synthetic (seeded Gaussian test vectors, workload of the config)",
         "config": {"workload": w.name, "n": w.n, "k": w.k, "n_omega": w.n_omega, "variant": w.variant,
                    "steps_per_window": n_t, "h": h, "steps_per_march": steps_per_march(w, n_t),
@@ -648,7 +650,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(W.ALL), default="c4")
     ap.add_argument("--step", choices=["march", "rsvd"], default="march")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default=None)
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default=None,
+                    help="bf16: the 3-D workload's march state stored in BF16 (arithmetic in FP32)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement (<= --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

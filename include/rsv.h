@@ -57,8 +57,13 @@ typedef enum {
 
 typedef enum {
   RSV_PREC_FP64 = 0, /* everything in FP64; parity path                             */
-  RSV_PREC_FP32 = 1  /* state, operator and products in FP32; DFT accumulators and
+  RSV_PREC_FP32 = 1, /* state, operator and products in FP32; DFT accumulators and
                         the per-frequency QR/SVD glue in FP64                        */
+  RSV_PREC_BF16_STATE = 2 /* as RSV_PREC_FP32 (complex64 blocks), with the march state and
+                        stage inputs stored in BF16 (arithmetic, RK4 accumulator,
+                        forcing and snapshot tiles in FP32); ADV3D with nx a multiple
+                        of 4.  BF16 storage rounds to 2^-8 relative per step: use the
+                        FP64 refinement pass (rsv_refine_gains) for accurate gains    */
 } rsv_precision;
 
 typedef enum {

@@ -1,10 +1,13 @@
 // Operator kinds: construction of the device coefficient arrays and the
 // dispatch of one march tile / one operator application to each kind's
 // kernels.
+#include <cuda_bf16.h>
+
 #include <cstdlib>
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <type_traits>
 #include <vector>
 
 #include "rsv_ops.h"
@@ -183,6 +186,12 @@ int march_tile_kernels(rsv_operator op, int steps, int kg) {
       const char* e = getenv("RSV_STENCIL_FUSED");
       return (e != nullptr && e[0] == '1') ? steps + 1 : 4 * steps + 1;   // per-stage kernels by default
     }
+    case RSV_OP_ADV3D: {
+      const char* e = getenv("RSV_STENCIL3D_STAGED");
+      const bool pairs = op->prec == RSV_PREC_FP32 && !op->bf16_state && !(e != nullptr && e[0] == '1') &&
+                         op->nx % 4 == 0 && op->n < ((int64_t)1 << 31);
+      return pairs ? 2 * steps + 1 : 4 * steps + 1;   // two stage-pair kernels per step, or four stages
+    }
     default:
       return 4 * steps + 1;
   }
@@ -216,11 +225,15 @@ rsv_status prepare_coefficients(rsv_operator op, const void* fhat, int64_t f_str
 }
 
 namespace {
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
 template <typename T>
 __global__ void finite_kernel(const T* __restrict__ x, int64_t count, int* flag) {
   bool bad = false;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)x[e];
+    const double v = to_d(x[e]);
     if (!(fabs(v) < 1e300)) bad = true;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
@@ -232,7 +245,7 @@ __global__ void vec_sumsq_kernel(const T* __restrict__ x, int64_t vals_per_vec, 
   const T* xv = x + (int64_t)blockIdx.y * vals_per_vec;
   double acc = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < vals_per_vec; e += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)xv[e];
+    const double v = to_d(xv[e]);
     acc += v * v;
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -253,7 +266,7 @@ __global__ void inst_sumsq_kernel(const T* __restrict__ x, const int64_t* __rest
   const int64_t a = inst_off[inst] * vals_per_point, b = inst_off[inst + 1] * vals_per_point;
   double acc = 0.0;
   for (int64_t e = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < b; e += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)x[e];
+    const double v = to_d(x[e]);
     acc += v * v;
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -280,7 +293,10 @@ template <typename T>
 __global__ void probe_init_kernel(T* __restrict__ x, int64_t vals, uint64_t seed) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < vals; e += (int64_t)gridDim.x * blockDim.x) {
     const double u = 2.0 * (double)(splitmix64_at(seed, (uint64_t)e) >> 11) * 0x1.0p-53 - 1.0;
-    x[e] = (T)u;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value)
+      x[e] = __float2bfloat16((float)u);
+    else
+      x[e] = (T)u;
   }
 }
 }  // namespace
@@ -300,6 +316,8 @@ cudaError_t instance_sq_norms(rsv_operator op, int64_t n_end, double* d_out) {
   const int64_t* off = (const int64_t*)op->d_inst_off;
   if (op->prec == RSV_PREC_FP64)
     inst_sumsq_kernel<double><<<grid, 256, 0, op->stream>>>((const double*)st, off, vpp, d_out);
+  else if (op->bf16_state)
+    inst_sumsq_kernel<__nv_bfloat16><<<grid, 256, 0, op->stream>>>((const __nv_bfloat16*)st, off, vpp, d_out);
   else
     inst_sumsq_kernel<float><<<grid, 256, 0, op->stream>>>((const float*)st, off, vpp, d_out);
   return cudaGetLastError();
@@ -311,6 +329,8 @@ cudaError_t probe_initial_state(rsv_operator op, uint64_t seed) {
   const unsigned blocks = (unsigned)std::min<int64_t>((vals + 255) / 256, 8 * std::max(op->sm_count, 1));
   if (op->prec == RSV_PREC_FP64)
     probe_init_kernel<double><<<blocks, 256, 0, op->stream>>>((double*)op->ws_state.ptr, vals, seed);
+  else if (op->bf16_state)
+    probe_init_kernel<__nv_bfloat16><<<blocks, 256, 0, op->stream>>>((__nv_bfloat16*)op->ws_state.ptr, vals, seed);
   else
     probe_init_kernel<float><<<blocks, 256, 0, op->stream>>>((float*)op->ws_state.ptr, vals, seed);
   return cudaGetLastError();
@@ -329,6 +349,8 @@ cudaError_t state_sq_norms(rsv_operator op, int kg, int64_t n_end, double* d_out
   dim3 grid(std::max(bx, 1u), (unsigned)kg);
   if (op->prec == RSV_PREC_FP64)
     vec_sumsq_kernel<double><<<grid, 256, 0, op->stream>>>((const double*)st, vals, d_out);
+  else if (op->bf16_state)   // BF16 state: vector v's values at v * vals BF16 elements
+    vec_sumsq_kernel<__nv_bfloat16><<<grid, 256, 0, op->stream>>>((const __nv_bfloat16*)st, vals, d_out);
   else
     vec_sumsq_kernel<float><<<grid, 256, 0, op->stream>>>((const float*)st, vals, d_out);
   return cudaGetLastError();
@@ -339,6 +361,8 @@ cudaError_t check_finite(rsv_operator op, const void* state, int64_t count, bool
   const unsigned blocks = (unsigned)std::min<int64_t>((vals + 255) / 256, 4 * std::max(op->sm_count, 1));
   if (op->prec == RSV_PREC_FP64)
     finite_kernel<double><<<blocks, 256, 0, op->stream>>>((const double*)state, vals, op->d_flag);
+  else if (op->bf16_state)
+    finite_kernel<__nv_bfloat16><<<blocks, 256, 0, op->stream>>>((const __nv_bfloat16*)state, vals, op->d_flag);
   else
     finite_kernel<float><<<blocks, 256, 0, op->stream>>>((const float*)state, vals, op->d_flag);
   return cudaGetLastError();

@@ -163,8 +163,10 @@ extern "C" const char* rsv_version(void) { return "rsv 0.2 (sm_103a)"; }
 extern "C" rsv_status rsv_create_operator(const rsv_operator_desc* d, void* stream, rsv_operator* out) {
   if (!d || !out) return fail(RSV_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
-  if (d->precision != RSV_PREC_FP64 && d->precision != RSV_PREC_FP32)
+  if (d->precision != RSV_PREC_FP64 && d->precision != RSV_PREC_FP32 && d->precision != RSV_PREC_BF16_STATE)
     return fail(RSV_ERR_INVALID_ARG, "unknown precision");
+  if (d->precision == RSV_PREC_BF16_STATE && !(d->kind == RSV_OP_ADV3D && d->nx % 4 == 0))
+    return fail(RSV_ERR_INVALID_ARG, "BF16 state is built for the ADV3D kind with nx a multiple of 4");
   if (!(d->dt > 0.0)) return fail(RSV_ERR_INVALID_ARG, "dt must be positive");
   if (d->scheme != RSV_SCHEME_RK4 && d->scheme != RSV_SCHEME_CN) return fail(RSV_ERR_INVALID_ARG, "unknown scheme");
   if (d->scheme == RSV_SCHEME_CN && d->kind != RSV_OP_GL1D)
@@ -172,7 +174,8 @@ extern "C" rsv_status rsv_create_operator(const rsv_operator_desc* d, void* stre
   rsv_operator op = new rsv_operator_s();
   op->kind = d->kind;
   op->scheme = d->scheme;
-  op->prec = d->precision;
+  op->prec = d->precision == RSV_PREC_FP64 ? RSV_PREC_FP64 : RSV_PREC_FP32;
+  op->bf16_state = d->precision == RSV_PREC_BF16_STATE;
   op->dt = d->dt;
   op->stream = (cudaStream_t)stream;
   {
@@ -242,7 +245,9 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
     path = op->scheme == RSV_SCHEME_CN ? "cuda-core crank-nicolson tile kernel" : "cuda-core tile kernel";
   if (op->kind == RSV_OP_ADV3D && op->prec == RSV_PREC_FP32) {
     const char* e = getenv("RSV_STENCIL3D_STAGED");
-    path = (e != nullptr && e[0] == '1') ? "cuda-core stages" : "cuda-core 3-D stage-pair kernels";
+    const bool pairs = !(e != nullptr && e[0] == '1') && !op->bf16_state && op->nx % 4 == 0 &&
+                       op->n < ((int64_t)1 << 31);
+    path = pairs ? "cuda-core 3-D stage-pair kernels" : (op->bf16_state ? "cuda-core stages, bf16 state" : "cuda-core stages");
   }
   if (op->kind == RSV_OP_ADR2D) {
     const char* e = getenv("RSV_STENCIL_FUSED");
@@ -258,7 +263,8 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
   snprintf(buf, (size_t)buflen,
            "kind=%s precision=%s n=%lld instances=%d path=%s contractions=%s resident_ctas=%d sms=%d tile=%d "
            "group=%d steps=%lld",
-           (op->kind >= 0 && op->kind < 4) ? kinds[op->kind] : "?", op->prec == RSV_PREC_FP64 ? "fp64" : "fp32",
+           (op->kind >= 0 && op->kind < 4) ? kinds[op->kind] : "?",
+           op->prec == RSV_PREC_FP64 ? "fp64" : (op->bf16_state ? "bf16-state" : "fp32"),
            (long long)op->n, op->n_inst, path, contract, op->tc_max_clusters, op->sm_count, op->last_tile,
            op->last_group, (long long)op->last_steps);
   return RSV_OK;

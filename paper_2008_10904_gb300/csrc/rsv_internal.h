@@ -91,7 +91,8 @@ struct Profiler {
 
 struct rsv_operator_s {
   int kind = 0;
-  int prec = 0;
+  int prec = 0;                          // RSV_PREC_FP64 or RSV_PREC_FP32 (also for BF16 state)
+  bool bf16_state = false;               // RSV_PREC_BF16_STATE: march state stored in BF16
   bool real_state = false;
   double dt = 0.0;
   int64_t n = 0;                        // state length (all instances, all components)

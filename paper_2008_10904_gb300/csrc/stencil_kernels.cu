@@ -18,6 +18,9 @@
 //   (A^T x)_p = (U_{p+1} x_{p+1} - U_{p-1} x_{p-1}) / (2 dx),
 // and the coupling -(u . grad)U (into component x only) becomes
 // -dU/dx_c * x_x into every component c.
+#include <cuda_bf16.h>
+
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <utility>
@@ -184,26 +187,48 @@ __device__ __forceinline__ void set4(float4& v, int q, float x) {
   if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
 }
 
-template <int STAGE>
-__device__ __forceinline__ void stage_update4(int64_t p, float4 k, const float* __restrict__ u, float* __restrict__ acc,
-                                              float* __restrict__ xout, float* __restrict__ ysnap, float h) {
+// State storage: FP32, or BF16 (RSV_PREC_BF16_STATE: storage only, arithmetic in FP32; four values
+// are 8 bytes).
+__device__ __forceinline__ float4 ld4s(const float* p) { return ld4(p); }
+__device__ __forceinline__ float4 ld4s(const __nv_bfloat16* p) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float lds(const float* p) { return *p; }
+__device__ __forceinline__ float lds(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void st4s(float* p, float4 v) { st4(p, v); }
+__device__ __forceinline__ void st4s(__nv_bfloat16* p, float4 v) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  uint2 o;
+  o.x = *reinterpret_cast<const uint32_t*>(&a);
+  o.y = *reinterpret_cast<const uint32_t*>(&b);
+  *reinterpret_cast<uint2*>(p) = o;
+}
+
+// Stage update of four values; u and the stage outputs in the state type S, accumulator, forcing
+// and snapshot in FP32.
+template <int STAGE, typename S>
+__device__ __forceinline__ void stage_update4(int64_t p, float4 k, const S* __restrict__ u, float* __restrict__ acc,
+                                              S* __restrict__ xout, float* __restrict__ ysnap, float h) {
   if (STAGE == 1) {
-    const float4 uu = ld4(u + p);
+    const float4 uu = ld4s(u + p);
     if (ysnap) st4(ysnap + p, uu);
-    st4(xout + p, make_float4(uu.x + 0.5f * h * k.x, uu.y + 0.5f * h * k.y, uu.z + 0.5f * h * k.z, uu.w + 0.5f * h * k.w));
+    st4s(xout + p, make_float4(uu.x + 0.5f * h * k.x, uu.y + 0.5f * h * k.y, uu.z + 0.5f * h * k.z, uu.w + 0.5f * h * k.w));
     const float c = h / 6.f;
     st4(acc + p, make_float4(uu.x + c * k.x, uu.y + c * k.y, uu.z + c * k.z, uu.w + c * k.w));
   } else if (STAGE == 2 || STAGE == 3) {
-    const float4 uu = ld4(u + p);
+    const float4 uu = ld4s(u + p);
     const float cx = STAGE == 2 ? 0.5f * h : h;
-    st4(xout + p, make_float4(uu.x + cx * k.x, uu.y + cx * k.y, uu.z + cx * k.z, uu.w + cx * k.w));
+    st4s(xout + p, make_float4(uu.x + cx * k.x, uu.y + cx * k.y, uu.z + cx * k.z, uu.w + cx * k.w));
     float4 a = ld4(acc + p);
     const float c = h / 3.f;
     st4(acc + p, make_float4(a.x + c * k.x, a.y + c * k.y, a.z + c * k.z, a.w + c * k.w));
   } else {
     const float4 a = ld4(acc + p);
     const float c = h / 6.f;
-    st4(xout + p, make_float4(a.x + c * k.x, a.y + c * k.y, a.z + c * k.z, a.w + c * k.w));
+    st4s(xout + p, make_float4(a.x + c * k.x, a.y + c * k.y, a.z + c * k.z, a.w + c * k.w));
   }
 }
 
@@ -241,15 +266,15 @@ __global__ void __launch_bounds__(256) adr2d_stage4_kernel(StGeom g, const float
     const float cc = cc0 - sponge<float>(i0 + q, j, g);
     set4(k, q, cw * left + ce * right + cy * (get4(sv, q) + get4(nv, q)) + cc * get4(c, q) + get4(fv, q));
   }
-  stage_update4<STAGE>(base + row + i0, k, u, acc, xout, ysnap, h);
+  stage_update4<STAGE, float>(base + row + i0, k, u, acc, xout, ysnap, h);
 }
 
 // Blocks are ordered with the vector index fastest, so the base-flow fields of a
 // cell block are read from HBM once and served from L2 to the other vectors.
-template <int STAGE>
-__global__ void __launch_bounds__(256) adv3d_stage4_kernel(StGeom g, const float* __restrict__ xin,
-                                                           const float* __restrict__ u, float* __restrict__ acc,
-                                                           const float* __restrict__ f, float* xout,
+template <int STAGE, typename S>
+__global__ void __launch_bounds__(256) adv3d_stage4_kernel(StGeom g, const S* __restrict__ xin,
+                                                           const S* __restrict__ u, float* __restrict__ acc,
+                                                           const float* __restrict__ f, S* xout,
                                                            float* __restrict__ ysnap, float h) {
   const int v = blockIdx.x % g.kg;
   const int cb = blockIdx.x / g.kg;
@@ -274,14 +299,14 @@ __global__ void __launch_bounds__(256) adv3d_stage4_kernel(StGeom g, const float
   float4 xc[3], k[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const float* x = xin + base + c * ncell;
-    const float4 cv = ld4(x + q0);
-    const float w = i0 > 0 ? x[q0 - 1] : 0.f;
-    const float e = i0 + 4 < nx ? x[q0 + 4] : 0.f;
-    const float4 sv = j > 0 ? ld4(x + q0 - nx) : zero;
-    const float4 nv = j < ny - 1 ? ld4(x + q0 + nx) : zero;
-    const float4 bv = kz > 0 ? ld4(x + q0 - (int64_t)nx * ny) : zero;
-    const float4 tv = kz < nz - 1 ? ld4(x + q0 + (int64_t)nx * ny) : zero;
+    const S* x = xin + base + c * ncell;
+    const float4 cv = ld4s(x + q0);
+    const float w = i0 > 0 ? lds(x + q0 - 1) : 0.f;
+    const float e = i0 + 4 < nx ? lds(x + q0 + 4) : 0.f;
+    const float4 sv = j > 0 ? ld4s(x + q0 - nx) : zero;
+    const float4 nv = j < ny - 1 ? ld4s(x + q0 + nx) : zero;
+    const float4 bv = kz > 0 ? ld4s(x + q0 - (int64_t)nx * ny) : zero;
+    const float4 tv = kz < nz - 1 ? ld4s(x + q0 + (int64_t)nx * ny) : zero;
     xc[c] = cv;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -320,7 +345,7 @@ __global__ void __launch_bounds__(256) adv3d_stage4_kernel(StGeom g, const float
       const float4 fv = ld4(f + p);
       kc = make_float4(kc.x + fv.x, kc.y + fv.y, kc.z + fv.z, kc.w + fv.w);
     }
-    stage_update4<STAGE>(p, kc, u, acc, xout, ysnap, h);
+    stage_update4<STAGE, S>(p, kc, u, acc, xout, ysnap, h);
   }
 }
 
@@ -577,12 +602,14 @@ cudaError_t launch_adr2d_step(rsv_operator op, const StGeom& g, const R* uin, R*
 // Cells outside the grid hold zero (homogeneous Dirichlet), in both rings.
 // ---------------------------------------------------------------------------
 constexpr int k3TX = 64, k3TY = 8, k3ZC = 16;
-constexpr int k3UW = k3TX + 4, k3UH = k3TY + 4;     // ring of the pair's stencil input (halo 2)
+constexpr int k3UW = k3TX + 8, k3UH = k3TY + 4;     // ring of the pair's stencil input: x from X0 - 4
+                                                    // (16-byte aligned rows), halo 2 used, y halo 2
 constexpr int k3XW = k3TX + 2, k3XH = k3TY + 2;     // ring of the intermediate stage (halo 1)
 constexpr int k3UP = k3UW * k3UH, k3XP = k3XW * k3XH;
 constexpr int k3Threads = 256;
 constexpr int k3S1 = (k3XP + k3Threads - 1) / k3Threads;   // first-stage cells per thread (3)
 constexpr int k3S2 = k3TX * k3TY / k3Threads;              // second-stage cells per thread (2)
+constexpr int k3Row4 = k3UW / 4;                           // 16-byte chunks per ring row (18)
 constexpr size_t k3Smem = sizeof(float) * (4 * 3 * (size_t)k3UP + 3 * 3 * (size_t)k3XP);
 
 struct Pair3D {
@@ -595,6 +622,7 @@ struct Pair3D {
   float* acc_out;      // pair A: accumulator
   float* ysnap;        // pair A: snapshot of u (nullable)
   float h;
+  int zchunks;         // z is cut into this many runs of planes, as even as possible
 };
 
 // Base flow at one cell, as the operator's fields hold it (U = erf(r / delta(x)) and its gradient):
@@ -603,13 +631,12 @@ struct Bf {
   float Uc, Uw, Ue, Ux, Uy, Uz;
 };
 
-// 7-point operator (forward or transposed) of component-interleaved shared-memory planes at local
-// (lx, ly) of a plane of width W; planes below, centre, above.
+// 7-point operator (forward or transposed) of component-interleaved shared-memory planes at index e
+// of a plane with rows of width W; planes below, centre, above.
 template <bool ADJ, int W, int PLANE>
 __device__ __forceinline__ void op3d_smem(const float* __restrict__ xb, const float* __restrict__ xc,
-                                          const float* __restrict__ xt, int lx, int ly, const Bf& bf, float cdx,
+                                          const float* __restrict__ xt, int e, const Bf& bf, float cdx,
                                           float idx2, float idy2, float idz2, float nu, float out[3]) {
-  const int e = ly * W + lx;
   float xcen[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -629,9 +656,9 @@ __device__ __forceinline__ void op3d_smem(const float* __restrict__ xb, const fl
   }
 }
 
-// Base-flow fields at grid cell q (i its x index), for the forward or transposed operator.
+// Base-flow fields at cell offset q (x index i), for the forward or transposed operator.
 template <bool ADJ>
-__device__ __forceinline__ Bf load_bf(const StGeom& g, int64_t q, int i, bool ok) {
+__device__ __forceinline__ Bf load_bf(const StGeom& g, int q, int i, bool ok) {
   const float* U = reinterpret_cast<const float*>(g.f0);
   const float* Ux = reinterpret_cast<const float*>(g.f1);
   const float* Uy = reinterpret_cast<const float*>(g.f2);
@@ -644,6 +671,12 @@ __device__ __forceinline__ Bf load_bf(const StGeom& g, int64_t q, int i, bool ok
   b.Uy = ok ? __ldg(Uy + q) : 0.f;
   b.Uz = ok ? __ldg(Uz + q) : 0.f;
   return b;
+}
+
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
 }
 
 // Per-thread registers of one plane's point inputs, loaded one plane ahead of their use.
@@ -659,14 +692,15 @@ struct Stage2In {
   Bf bf[k3S2];         // base flow
 };
 
+// Requires nx % 4 == 0 (16-byte rows of the input ring) and n < 2^31 (32-bit offsets in a vector).
 template <bool ADJ, bool PAIR_B, int MINB>
 __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, Pair3D P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);            // [4 planes][3 comps][k3UP]
   float* mid = ring + 4 * 3 * k3UP;                              // [3 planes][3 comps][k3XP]
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int64_t ncell = (int64_t)nx * ny * nz;
-  const int64_t plane = (int64_t)nx * ny;
+  const int ncell = nx * ny * nz;
+  const int plane = nx * ny;
   // block order: vector fastest (neighbouring tiles of all vectors in flight together), then x, y, z
   int b = blockIdx.x;
   const int v = b % g.kg;
@@ -675,14 +709,18 @@ __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, P
   const int X0 = (b % ntx) * k3TX;
   b /= ntx;
   const int Y0 = (b % nty) * k3TY;
-  const int z0 = (b / nty) * k3ZC;
-  const int z1 = min(z0 + k3ZC, nz);
+  const int cz = b / nty;
+  const int z0 = (int)((int64_t)cz * nz / P.zchunks);
+  const int z1 = (int)((int64_t)(cz + 1) * nz / P.zchunks);
   const int64_t base = (int64_t)v * g.n;
   const float* __restrict__ in = P.in + base;
-  const float* __restrict__ fa = P.fa;
-  const float* __restrict__ fb = P.fb;
-  const float* __restrict__ pu = P.u;
-  const float* __restrict__ pacc = P.acc;
+  const float* __restrict__ fa = P.fa ? P.fa + base : nullptr;
+  const float* __restrict__ fb = P.fb ? P.fb + base : nullptr;
+  const float* __restrict__ pu = PAIR_B ? P.u + base : nullptr;
+  const float* __restrict__ pacc = PAIR_B ? P.acc + base : nullptr;
+  float* __restrict__ out = P.out + base;
+  float* __restrict__ acc_out = PAIR_B ? nullptr : P.acc_out + base;
+  float* __restrict__ ysnap = P.ysnap ? P.ysnap + base : nullptr;
   const float cdx = 0.5f / (float)g.dx, idx2 = 1.f / ((float)g.dx * (float)g.dx);
   const float idy2 = 1.f / ((float)g.dy * (float)g.dy), idz2 = 1.f / ((float)g.dz * (float)g.dz);
   const float nu = (float)g.visc;
@@ -691,53 +729,72 @@ __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, P
   const float c2 = PAIR_B ? h / 6.f : 0.5f * h;  // pair A: x3 = u + h/2 k2; pair B: u' = ... + h/6 k4
   const int tid = threadIdx.x;
 
-  // asynchronous copy of plane kz of the stencil input (tile + 2 halo cells) into ring slot kz & 3
+  // per-thread cells, fixed over the planes: (x, y) offset in a plane (-1 outside the grid), x index,
+  // and the shared-memory indices in the input ring and the intermediate ring
+  int xy1[k3S1], gi1[k3S1], eu1[k3S1];
+#pragma unroll
+  for (int sl = 0; sl < k3S1; ++sl) {
+    const int e = tid + sl * k3Threads;
+    const int lx = e % k3XW, ly = e / k3XW;
+    const int gi = X0 - 1 + lx, gj = Y0 - 1 + ly;
+    const bool ok = e < k3XP && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+    xy1[sl] = ok ? gj * nx + gi : -1;
+    gi1[sl] = gi;
+    eu1[sl] = (ly + 1) * k3UW + lx + 3;       // ring x index = gi - (X0 - 4)
+  }
+  int xy2[k3S2], gi2[k3S2];
+#pragma unroll
+  for (int sl = 0; sl < k3S2; ++sl) {
+    const int e = tid + sl * k3Threads;
+    const int gi = X0 + e % k3TX, gj = Y0 + e / k3TX;
+    xy2[sl] = (gi < nx && gj < ny) ? gj * nx + gi : -1;
+    gi2[sl] = gi;
+  }
+
+  // asynchronous copy of plane kz of the stencil input into ring slot kz & 3: rows of 72 floats from
+  // x = X0 - 4, 16-byte chunks, each wholly inside or outside the grid (nx and X0 are multiples of 4)
   auto load_plane = [&](int kz) {
     float* dst = ring + (size_t)(kz & 3) * 3 * k3UP;
     const bool zin = kz >= 0 && kz < nz;
-    for (int e = tid; e < 3 * k3UP; e += k3Threads) {
-      const int c = e / k3UP, r = e - c * k3UP;
-      const int gi = X0 - 2 + r % k3UW, gj = Y0 - 2 + r / k3UW;
-      if (zin && gi >= 0 && gi < nx && gj >= 0 && gj < ny)
-        cp_async_elem(dst + e, in + c * ncell + (int64_t)kz * plane + (int64_t)gj * nx + gi);
+    for (int e = tid; e < 3 * k3UH * k3Row4; e += k3Threads) {
+      const int row = e / k3Row4, ch = e - row * k3Row4;      // row = c * k3UH + ly
+      const int c = row / k3UH, ly = row - c * k3UH;
+      const int gj = Y0 - 2 + ly, gx = X0 - 4 + 4 * ch;
+      float* d = dst + c * k3UP + ly * k3UW + 4 * ch;
+      if (zin && gj >= 0 && gj < ny && gx >= 0 && gx < nx)
+        cp_async16(d, in + c * ncell + kz * plane + gj * nx + gx);
       else
-        dst[e] = 0.f;
+        *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  // point inputs of the first stage on plane kz (tile + 1 halo), into registers
   auto fetch1 = [&](int kz, Stage1In& r) {
+    const bool zin = kz >= 0 && kz < nz;
 #pragma unroll
     for (int sl = 0; sl < k3S1; ++sl) {
-      const int e = tid + sl * k3Threads;
-      const int gi = X0 - 1 + e % k3XW, gj = Y0 - 1 + e / k3XW;
-      const bool ok = e < k3XP && kz >= 0 && kz < nz && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
-      const int64_t qc = (int64_t)kz * plane + (int64_t)gj * nx + gi;
-      const int64_t q = base + qc;
+      const bool ok = zin && xy1[sl] >= 0;
+      const int q = kz * plane + xy1[sl];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         r.f[sl][c] = (ok && fa) ? __ldg(fa + q + c * ncell) : 0.f;
         r.u[sl][c] = (PAIR_B && ok) ? __ldg(pu + q + c * ncell) : 0.f;
       }
-      r.bf[sl] = load_bf<ADJ>(g, qc, gi, ok);
+      r.bf[sl] = load_bf<ADJ>(g, q, gi1[sl], ok);
     }
   };
-  // point inputs of the second stage on plane kz (the tile), into registers
   auto fetch2 = [&](int kz, Stage2In& r) {
+    const bool zin = kz >= z0 && kz < z1;
 #pragma unroll
     for (int sl = 0; sl < k3S2; ++sl) {
-      const int e = tid + sl * k3Threads;
-      const int gi = X0 + e % k3TX, gj = Y0 + e / k3TX;
-      const bool ok = kz >= z0 && kz < z1 && gi < nx && gj < ny;
-      const int64_t qc = (int64_t)kz * plane + (int64_t)gj * nx + gi;
-      const int64_t q = base + qc;
+      const bool ok = zin && xy2[sl] >= 0;
+      const int q = kz * plane + xy2[sl];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         r.f[sl][c] = (ok && fb) ? __ldg(fb + q + c * ncell) : 0.f;
         r.u[sl][c] = (PAIR_B && ok) ? __ldg(pu + q + c * ncell) : 0.f;
         r.a[sl][c] = (PAIR_B && ok) ? __ldg(pacc + q + c * ncell) : 0.f;
       }
-      r.bf[sl] = load_bf<ADJ>(g, qc, gi, ok);
+      r.bf[sl] = load_bf<ADJ>(g, q, gi2[sl], ok);
     }
   };
 
@@ -752,16 +809,13 @@ __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, P
     for (int sl = 0; sl < k3S1; ++sl) {
       const int e = tid + sl * k3Threads;
       if (e >= k3XP) break;
-      const int lx = e % k3XW, ly = e / k3XW;
-      const int gi = X0 - 1 + lx, gj = Y0 - 1 + ly;
       float xo[3] = {0.f, 0.f, 0.f};
-      if (zin && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+      if (zin && xy1[sl] >= 0) {
         float k[3];
-        op3d_smem<ADJ, k3UW, k3UP>(xb, xc, xt, lx + 1, ly + 1, r.bf[sl], cdx, idx2, idy2, idz2, nu, k);
-        const int eu = (ly + 1) * k3UW + lx + 1;
+        op3d_smem<ADJ, k3UW, k3UP>(xb, xc, xt, eu1[sl], r.bf[sl], cdx, idx2, idy2, idz2, nu, k);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float uu = PAIR_B ? r.u[sl][c] : xc[c * k3UP + eu];
+          const float uu = PAIR_B ? r.u[sl][c] : xc[c * k3UP + eu1[sl]];
           xo[c] = uu + c1 * (k[c] + r.f[sl][c]);
         }
       }
@@ -778,28 +832,27 @@ __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, P
     const float* uc = ring + (size_t)(kz & 3) * 3 * k3UP;
 #pragma unroll
     for (int sl = 0; sl < k3S2; ++sl) {
+      if (xy2[sl] < 0) continue;
       const int e = tid + sl * k3Threads;
       const int tx = e % k3TX, ty = e / k3TX;
-      const int gi = X0 + tx, gj = Y0 + ty;
-      if (gi >= nx || gj >= ny) continue;
-      const int64_t q = (int64_t)kz * plane + (int64_t)gj * nx + gi;
-      float k[3];
-      op3d_smem<ADJ, k3XW, k3XP>(mb, mc, mt, tx + 1, ty + 1, r.bf[sl], cdx, idx2, idy2, idz2, nu, k);
       const int em = (ty + 1) * k3XW + tx + 1;
+      const int q = kz * plane + xy2[sl];
+      float k[3];
+      op3d_smem<ADJ, k3XW, k3XP>(mb, mc, mt, em, r.bf[sl], cdx, idx2, idy2, idz2, nu, k);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const int64_t pidx = base + c * ncell + q;
+        const int pidx = c * ncell + q;
         const float xm = mc[c * k3XP + em];
         if (!PAIR_B) {
-          const float uu = uc[c * k3UP + (ty + 2) * k3UW + tx + 2];
+          const float uu = uc[c * k3UP + (ty + 2) * k3UW + tx + 4];
           const float kk = k[c] + r.f[sl][c];
-          P.out[pidx] = uu + c2 * kk;                                       // x3
-          P.acc_out[pidx] = uu + (xm - uu) * (1.f / 3.f) + (h / 3.f) * kk;   // u + h/6 k1 + h/3 k2
-          if (P.ysnap) P.ysnap[pidx] = uu;
+          out[pidx] = uu + c2 * kk;                                       // x3
+          acc_out[pidx] = uu + (xm - uu) * (1.f / 3.f) + (h / 3.f) * kk;   // u + h/6 k1 + h/3 k2
+          if (ysnap) ysnap[pidx] = uu;
         } else {
           const float uu = r.u[sl][c];
-          const float a = r.a[sl][c] + (xm - uu) * (1.f / 3.f);             // + h/3 k3
-          P.out[pidx] = a + c2 * (k[c] + r.f[sl][c]);                       // + h/6 k4
+          const float a = r.a[sl][c] + (xm - uu) * (1.f / 3.f);           // + h/3 k3
+          out[pidx] = a + c2 * (k[c] + r.f[sl][c]);                       // + h/6 k4
         }
       }
     }
@@ -841,20 +894,44 @@ int pair3d_minb() {
   return v;
 }
 
+// Number of z runs: as many CTAs as fill whole waves of the resident CTAs (runs of at least 4 planes,
+// at most 64 of them), so that the last wave is not left mostly idle.
+int pair3d_zchunks(int per_chunk, int nz, int resident) {
+  int best = std::max(1, (nz + k3ZC - 1) / k3ZC);
+  double best_eff = -1.0;
+  for (int nc = std::max(1, nz / 64); nc <= std::min(64, std::max(1, nz / 4)); ++nc) {
+    const double waves = (double)per_chunk * nc / std::max(resident, 1);
+    const double eff = waves / std::ceil(waves) - 0.002 * nc;     // prefer fewer runs (less halo work)
+    if (eff > best_eff) {
+      best_eff = eff;
+      best = nc;
+    }
+  }
+  return best;
+}
+
 template <bool ADJ, bool PAIR_B, int MINB>
-cudaError_t launch_pair3d_minb(rsv_operator op, const StGeom& g, const Pair3D& P) {
+cudaError_t launch_pair3d_minb(rsv_operator op, const StGeom& g, const Pair3D& P0) {
   static int attr_dev[64] = {0};
+  static int resident_dev[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_dev[dev]) {
     cudaError_t e = cudaFuncSetAttribute(adv3d_pair_kernel<ADJ, PAIR_B, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3Smem);
     if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adv3d_pair_kernel<ADJ, PAIR_B, MINB>, k3Threads,
+                                                      k3Smem);
+    if (e != cudaSuccess) return e;
+    resident_dev[dev] = std::max(1, per_sm) * std::max(1, op->sm_count);
     attr_dev[dev] = 1;
   }
+  const int resident = (dev >= 0 && dev < 64) ? resident_dev[dev] : op->sm_count;
   const unsigned ntx = (unsigned)((g.nx + k3TX - 1) / k3TX), nty = (unsigned)((g.ny + k3TY - 1) / k3TY);
-  const unsigned ntz = (unsigned)((g.nz + k3ZC - 1) / k3ZC);
-  const unsigned blocks = ntx * nty * ntz * (unsigned)g.kg;
+  Pair3D P = P0;
+  P.zchunks = pair3d_zchunks((int)(ntx * nty) * g.kg, g.nz, resident);
+  const unsigned blocks = ntx * nty * (unsigned)P.zchunks * (unsigned)g.kg;
   adv3d_pair_kernel<ADJ, PAIR_B, MINB><<<blocks, k3Threads, k3Smem, op->stream>>>(g, P);
   return cudaGetLastError();
 }
@@ -894,7 +971,14 @@ cudaError_t launch_stage(rsv_operator op, const StGeom& g, const R* xin, const R
       adr2d_stage4_kernel<STAGE><<<grid, dim3(32, 8), 0, op->stream>>>(g, xi, uu, ac, ff, xo, ys, (float)h);
     } else {
       const unsigned blocks = gx * (unsigned)((g.ny * g.nz + 7) / 8) * (unsigned)g.kg;
-      adv3d_stage4_kernel<STAGE><<<blocks, dim3(32, 8), 0, op->stream>>>(g, xi, uu, ac, ff, xo, ys, (float)h);
+      if (op->bf16_state) {
+        // xin, u, xout hold BF16 values at the FP32 slots' addresses
+        adv3d_stage4_kernel<STAGE, __nv_bfloat16><<<blocks, dim3(32, 8), 0, op->stream>>>(
+            g, reinterpret_cast<const __nv_bfloat16*>(xin), reinterpret_cast<const __nv_bfloat16*>(u), ac, ff,
+            reinterpret_cast<__nv_bfloat16*>(xout), ys, (float)h);
+      } else {
+        adv3d_stage4_kernel<STAGE, float><<<blocks, dim3(32, 8), 0, op->stream>>>(g, xi, uu, ac, ff, xo, ys, (float)h);
+      }
     }
     return cudaGetLastError();
   }
@@ -1010,7 +1094,8 @@ cudaError_t stencil_march_tile(rsv_operator op, const MarchTile& t, void* state,
     if (e == cudaSuccess) e = check_finite(op, u, rows, true);
     return e;
   }
-  if (sizeof(R) == 4 && op->kind == RSV_OP_ADV3D && adv3d_pairs_enabled()) {
+  if (sizeof(R) == 4 && op->kind == RSV_OP_ADV3D && adv3d_pairs_enabled() && !op->bf16_state &&
+      op->nx % 4 == 0 && op->n < ((int64_t)1 << 31)) {
     // two fused stage pairs per step; the state ping-pongs between u and xb, x3 lives in xa
     float* cur = reinterpret_cast<float*>(u);
     float* nxt = reinterpret_cast<float*>(xb);

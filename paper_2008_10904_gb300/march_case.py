@@ -1,7 +1,7 @@
 """One direct (or adjoint) march of a named workload, for profilers.
 
   python -m paper_2008_10904_gb300.march_case --workload c3 [--k 16] [--n-omega 8] [--tile 16]
-         [--precision fp32|fp64] [--adjoint] [--repeat 2] [--full-schedule]
+         [--precision fp32|fp64|bf16] [--adjoint] [--repeat 2] [--full-schedule]
 
 Runs the workload's operator through rsv_march_direct / rsv_march_adjoint
 with a seeded Gaussian test block drawn on the device, optionally cut to
@@ -33,7 +33,7 @@ def main(argv=None):
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--n-omega", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "bf16"], default="fp32")
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--full-schedule", action="store_true")
@@ -55,8 +55,8 @@ def main(argv=None):
     else:
         w = W.Workload(full.name, full.system, om, full.dt, k, "trm", tail_steps=0,
                        real_state=full.real_state, seed=full.seed)
-    prec = rsv.RSV_PREC_FP32 if args.precision == "fp32" else rsv.RSV_PREC_FP64
-    cdt = torch.complex64 if args.precision == "fp32" else torch.complex128
+    prec = {"fp32": rsv.RSV_PREC_FP32, "fp64": rsv.RSV_PREC_FP64, "bf16": rsv.RSV_PREC_BF16_STATE}[args.precision]
+    cdt = torch.complex128 if args.precision == "fp64" else torch.complex64
     dense = W.hermite_gl_matrix(w.system) if type(w.system).__name__ == "Dense" else None
     op = rsv.create_for_workload(w, prec, dense_matrix=dense)
     n_t, h = rsv.rsv_set_frequencies(op, w.omegas)

@@ -20,7 +20,7 @@ RSV_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "NOT_COMMENSURATE", 4: "DIVERGED", 5: "TIMEOUT",
           6: "OOM", 7: "CUDA", 8: "STATE"}
 RSV_OP_GL1D, RSV_OP_DENSE, RSV_OP_ADR2D, RSV_OP_ADV3D = 0, 1, 2, 3
-RSV_PREC_FP64, RSV_PREC_FP32 = 0, 1
+RSV_PREC_FP64, RSV_PREC_FP32, RSV_PREC_BF16_STATE = 0, 1, 2
 RSV_SSRM, RSV_TRM = 0, 1
 RSV_SCHEME_RK4, RSV_SCHEME_CN = 0, 1
 

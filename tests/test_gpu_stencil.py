@@ -198,8 +198,8 @@ def test_adr2d_step_paths(rsv, make, prec, adjoint, path, monkeypatch):
 
 
 def _adv_multi(variant="trm", k=2):
-    """Several fused-pair tiles in x and y (64 x 8), ragged, and two z chunks (16 + 4 planes)."""
-    sysm = W.ADV3D(nx=70, ny=11, nz=20, lx=20.0, ly=10.0, lz=10.0, visc=0.02)
+    """Two fused-pair tiles in x (64 + 8 cells) and y (8 + 3), and two z chunks (16 + 4 planes); nx a multiple of 4."""
+    sysm = W.ADV3D(nx=72, ny=11, nz=20, lx=20.0, ly=10.0, lz=10.0, visc=0.02)
     om = np.array([0.04 * np.pi * 5 * j for j in range(6)])
     dx = sysm.lx / (sysm.nx + 1)
     return W.Workload("adv_multi", sysm, om, 0.5 * dx, k, variant, n_transient_windows=1, tail_steps=30,
