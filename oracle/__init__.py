@@ -20,6 +20,12 @@ Layout of the oracle, each module following the paper's statement:
                the exact resolvent of the RK4-discretised system
   rsvd         power iteration with the gain estimate of App. A Eq. (tildeSig) and
                the block (randomized-SVD) form used for the gains and modes
+  weighted     weighted (B, C, W) resolvent and its SVD (Sec. 2.1)
+  arnoldi      Arnoldi / Krylov suboptimal gains on the steady-state method (App. A)
+  series       the transient-response method in time-series form (Sec. 2.2):
+               series-driven runs, snapshot interpolation (App. C), FIR
+               flattening (App. B), Fourier transforms at any frequency and the
+               TRM power iteration
 
 Parity status: every function is pinned by the not-gpu tests in
 ``tests/test_oracle_*.py`` (closed forms, convergence orders, identities,
