@@ -214,6 +214,8 @@ def load_peaks():
 #   1-D march    gl1d_tile_c5.txt: one 127-step launch, 754.9 MB read + 344.4 MB written
 #   2-D march    adr2d_stage_c3.txt: the four stage kernels of one step at 16 vectors,
 #                558.5 MB per step, scaled by 255 steps (traffic per step is constant)
+#   3-D march    adv3d_pair_c4.txt: the two stage-pair kernels of one step at 2 vectors,
+#                1348.4 MB per step, scaled by 255 steps
 TRAFFIC = {
     ("dense_hermite_gl_n1024_k32_w256_trm", "march", 256, 32768):
         {"bytes": 108.98e6, "src": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"},
@@ -221,6 +223,8 @@ TRAFFIC = {
         {"bytes": 1.0993e9, "src": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"},
     ("adr2d_1024x512_k16_w128_ssrm", "march", 255, 8388608):
         {"bytes": 255 * 558.5e6, "src": "ncu dram bytes of the four stage kernels of one step x 255 steps"},
+    ("adv3d_256x128x128x3_k8_w64_ssrm", "march", 255, 25165824):
+        {"bytes": 255 * 1348.4e6, "src": "ncu dram bytes of the two stage-pair kernels of one step x 255 steps"},
 }
 
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
@@ -239,8 +243,9 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
                  and written once, (3S + 3) state passes per tile;
                  2-D whole-step kernel: 6 state passes per step (state read and written,
                  forcing read at the three stage times, snapshot written);
-                 per-stage kernels: 15 state passes per step (12 for four stage read/write
-                 pairs, 2 forcing reads, 1 snapshot write)
+                 per-stage and stage-pair kernels (2-D, 3-D): 15 state passes per step, the
+                 algorithmic model of one RK4 step (12 for four stage read/write pairs,
+                 2 forcing reads, 1 snapshot write), whatever the kernels actually move
     """
     peaks = load_peaks()
     avg_s = ms_total / max(groups, 1) / 1e3
