@@ -317,6 +317,99 @@ rsv_status rsv_orthonormalize(rsv_operator op, void* block, int32_t k, double* r
  * act on real and imaginary parts alike).  For testing the operator kernels. */
 rsv_status rsv_apply_operator(rsv_operator op, const void* x, int32_t k, int32_t adjoint, void* y);
 
+/* ---------------------------------------------------------------------------
+ * Transient-response method in time-series form (Sec. 2.2 with App. B and C).
+ *
+ * A run is driven by a sampled series instead of Fourier coefficients: its
+ * forcing at the stage times of each step (RK4: t_n, t_n + h/2, t_n + h;
+ * Crank-Nicolson: t_n, t_n + h) is the App. C interpolant of the input series,
+ * whose samples lie every `every` steps from t = 0, and is zero after the last
+ * sample; the state is recorded every `every` steps.  Series are device arrays
+ * [n_snap][k][n] of the state's element type: complex (re, im) for complex-
+ * state kinds, real for real-state kinds, FP64 or FP32 by the operator's
+ * precision.  The time step is the operator's h (rsv_set_frequencies must come
+ * first).  Kinds: GL1D (RK4 or Crank-Nicolson), ADR2D and ADV3D (RK4); not the
+ * dense kind, BF16 state or operators with rsv_set_weights.
+ * ------------------------------------------------------------------------- */
+typedef enum { RSV_INTERP_C0 = 0, RSV_INTERP_C1 = 1, RSV_INTERP_C2 = 2 } rsv_interp;
+
+typedef struct {
+  int32_t every;      /* steps between input samples and between recorded snapshots (>= 1) */
+  int32_t interp;     /* rsv_interp: C0 linear, C1 cubic Hermite, C2 quintic Hermite (App. C) */
+  double tail_tol;    /* truncation (Sec. 2.2): vector v's record ends at the first snapshot at or
+                         after the end of its forcing whose norm is <= tail_tol x the largest norm of
+                         its snapshots so far; later snapshots are zero.  0: no truncation. */
+} rsv_series_opts;
+
+/* One series-driven run.  u(0) = init (device [k][n], nullable: zero), forcing
+ * from `forcing` (device [n_in][k][n], nullable; sample i is read from row
+ * n_in - 1 - i when reverse_in = 1, the time reversal that turns a direct
+ * run's output into its adjoint run's forcing, Sec. 2.1).  adjoint = 1 marches
+ * with A^H.  out (device [n_out_max][k][n], must not alias forcing): snapshot j
+ * = u(j every h), j = 0 the initial state.  The run ends when every vector has
+ * stopped (tail_tol) or after n_out_max snapshots.  *n_out (host): snapshots
+ * written, rows >= *n_out untouched.  stops (host [k], nullable): the
+ * snapshot at which each vector stopped, -1 if it did not.  Errors:
+ * INVALID_ARG, STATE, DIVERGED, CUDA, OOM. */
+rsv_status rsv_series_march(rsv_operator op, int32_t adjoint, int32_t k, const void* init, const void* forcing,
+                            int64_t n_in, int32_t reverse_in, const rsv_series_opts* opts, void* out,
+                            int64_t n_out_max, int64_t* n_out, int64_t* stops);
+
+/* Fourier transform of a series at arbitrary frequencies by the rectangle rule
+ * (Sec. 2.1 Eq. (fourier), the sign of du/dt = A u + f):
+ *   out[j][v][p] = d sum_i x[i][v][p] exp(-i omega_j (t0 + i d)).
+ * series: device [n_snap][k][n] (state element type); omega: host
+ * [n_omega]; out: device [n_omega][k][n] complex of the operator's precision.
+ * Accumulated in FP64.  Errors: INVALID_ARG, CUDA, OOM. */
+rsv_status rsv_series_fourier(rsv_operator op, const void* series, int64_t n_snap, int32_t k, double d,
+                              double t0, const double* omega, int32_t n_omega, void* out);
+
+/* FIR filtering of a series (App. B), the whole convolution:
+ *   out[m][v][p] = sum_j phi_v[j] x[m - j][v][p],  0 <= m < n_in + order,
+ * phi_v = taps[v] (reverse_taps = 0) or taps[v] reversed (phi_v[j] =
+ * taps[v][order - j]; filtering a time-reversed series: reverse(phi * x) =
+ * reversed(phi) * reverse(x)).  taps: host [k][order + 1] complex128 (re, im);
+ * for real-state operators the taps must be real.  in: device [n_in][k][n];
+ * out: device [n_in + order][k][n], must not alias in.  Errors: INVALID_ARG,
+ * CUDA, OOM. */
+rsv_status rsv_series_filter(rsv_operator op, const void* in, int64_t n_in, int32_t k, const double* taps,
+                             int32_t order, int32_t reverse_taps, void* out);
+
+/* Linear-phase FIR filter by frequency sampling with a Hamming window (App. B):
+ * the amplitude A(w) is given at n_pts ascending frequencies w_pts (host),
+ * linear in between and constant beyond; if every w_pts >= 0 it is mirrored
+ * to negative frequencies (real taps), otherwise it is taken over signed
+ * frequencies (complex taps, for complex signals).  The spectrum
+ * A(w) exp(-i w order d / 2) on the 8 (order + 1)-point grid of spacing
+ * 2 pi / (8 (order + 1) d) is transformed back and its first order + 1 points
+ * are windowed.  order even; taps: host [order + 1] complex128 (re, im).
+ * Host computation, no device use.  Errors: INVALID_ARG. */
+rsv_status rsv_fir_design(int32_t order, double d, const double* w_pts, const double* amp, int32_t n_pts,
+                          double* taps);
+
+typedef struct {
+  rsv_series_opts series;
+  int32_t n_iter;        /* power iterations (>= 1) */
+  int32_t filter_order;  /* order of the flattening filter, even; 0: no filter, scalar normalisation */
+  int64_t n_snap_max;    /* snapshot capacity of each run's record */
+} rsv_trm_opts;
+
+/* Power iteration on R^H R by the transient-response method (Sec. 2.2, App. A
+ * Eqs. (iteration), (tildeSig)), each of the k vectors independently.
+ * Iteration 0 starts from the impulse f0 delta(t), applied as u(0) = f0
+ * (device [k][n], state element type).  Each iteration: a direct run, an
+ * adjoint run forced by the direct output reversed in time, w = the adjoint
+ * output reversed back; the gain estimate sigma(w)^2 = |w_hat(w)| / |f_hat(w)|
+ * at the n_omega frequencies omega (host); the next forcing is w filtered by
+ * the FIR filter of amplitude 1 / |w_hat(w)| at those frequencies (App. B),
+ * or, with filter_order = 0, w / max_w |w_hat(w)|.  gains: host
+ * [n_iter][n_omega][k]; w_hat (device [n_omega][k][n] complex, nullable): the
+ * last iteration's w_hat, the direction of the leading forcing mode, with w
+ * on the time axis t_i = i d (d = every h).  Errors: those of the runs, and
+ * INVALID_ARG when a record fills n_snap_max before it is negligible. */
+rsv_status rsv_trm_power_iteration(rsv_operator op, const void* f0, int32_t k, const double* omega,
+                                   int32_t n_omega, const rsv_trm_opts* opts, double* gains, void* w_hat);
+
 /* Kernel-time accounting.  With enable = 1 the operator brackets each group
  * of device launches of one kind with CUDA events on its stream, grouped by
  * category: 0 synthesis, 1 march (operator stages of one time tile),

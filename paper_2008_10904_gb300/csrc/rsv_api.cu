@@ -115,8 +115,9 @@ using namespace rsv;
 
 rsv_operator_s::~rsv_operator_s() {
   for (void* p : dev) cudaFree(p);
-  Workspace* ws[] = {&ws_state, &ws_ftile, &ws_ysnap, &ws_acc, &ws_norm, &ws_glue_a, &ws_glue_b,
-                     &ws_gram,  &ws_small, &ws_coef,  &ws_coef2, &ws_tcb};
+  Workspace* ws[] = {&ws_state, &ws_ftile, &ws_ysnap, &ws_acc,   &ws_norm,  &ws_glue_a, &ws_glue_b,
+                     &ws_gram,  &ws_small, &ws_coef,  &ws_coef2, &ws_tcb,   &ws_ser_e, &ws_ser_t,
+                     &ws_ser_y, &ws_ser_z, &ws_ser_g, &ws_ser_f, &ws_ser_n};
   for (Workspace* w : ws)
     if (w->ptr) cudaFree(w->ptr);
   if (d_tw) cudaFree(d_tw);

@@ -152,6 +152,9 @@ struct rsv_operator_s {
   // march workspace (grown on demand)
   rsv::Workspace ws_state, ws_ftile, ws_ysnap, ws_acc, ws_norm, ws_glue_a, ws_glue_b, ws_gram, ws_small;
   rsv::Workspace ws_coef, ws_coef2, ws_tcb;
+  // time-series runs (series.cu): Fourier table, filter taps, the TRM power iteration's records
+  // (direct output, adjoint output, next forcing), its FP64 Fourier block and norms
+  rsv::Workspace ws_ser_e, ws_ser_t, ws_ser_y, ws_ser_z, ws_ser_g, ws_ser_f, ws_ser_n;
   bool tc_contract_disabled = false;   // keep the synthesis / analysis on the CUDA cores
   int* d_flag = nullptr;
   rsv::Profiler prof;

@@ -23,6 +23,8 @@ RSV_OP_GL1D, RSV_OP_DENSE, RSV_OP_ADR2D, RSV_OP_ADV3D = 0, 1, 2, 3
 RSV_PREC_FP64, RSV_PREC_FP32, RSV_PREC_BF16_STATE = 0, 1, 2
 RSV_SSRM, RSV_TRM = 0, 1
 RSV_SCHEME_RK4, RSV_SCHEME_CN = 0, 1
+RSV_INTERP_C0, RSV_INTERP_C1, RSV_INTERP_C2 = 0, 1, 2
+_INTERP = {"c0": RSV_INTERP_C0, "c1": RSV_INTERP_C1, "c2": RSV_INTERP_C2}
 
 
 class RsvError(RuntimeError):
@@ -53,6 +55,15 @@ class rsv_march_opts(ctypes.Structure):
                 ("tail_steps", ctypes.c_int64), ("tile_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("tail_tol", ctypes.c_double), ("decay_tol", ctypes.c_double), ("decay_max_steps", ctypes.c_int64),
                 ("decay_seed", ctypes.c_uint64)]
+
+
+class rsv_series_opts(ctypes.Structure):
+    _fields_ = [("every", ctypes.c_int32), ("interp", ctypes.c_int32), ("tail_tol", ctypes.c_double)]
+
+
+class rsv_trm_opts(ctypes.Structure):
+    _fields_ = [("series", rsv_series_opts), ("n_iter", ctypes.c_int32), ("filter_order", ctypes.c_int32),
+                ("n_snap_max", ctypes.c_int64)]
 
 
 _lib = None
@@ -92,6 +103,23 @@ _ENTRY_POINTS = {
                                           ctypes.POINTER(ctypes.c_double)]),
     "rsv_apply_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_void_p]),
+    "rsv_series_march": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.POINTER(rsv_series_opts), ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "rsv_series_fourier": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_int32, ctypes.c_void_p]),
+    "rsv_series_filter": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_void_p]),
+    "rsv_fir_design": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "rsv_trm_power_iteration": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                               ctypes.POINTER(rsv_trm_opts), ctypes.POINTER(ctypes.c_double),
+                                               ctypes.c_void_p]),
     "rsv_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "rsv_profile_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "rsv_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
@@ -274,6 +302,62 @@ def rsv_orthonormalize(op: Operator, block, k: int, r_factor: np.ndarray | None 
 
 def rsv_apply_operator(op: Operator, x, k: int, adjoint: bool, y):
     _check(_lib.rsv_apply_operator(op.handle, _ptr(x), int(k), int(bool(adjoint)), _ptr(y)))
+
+
+def _f64(x):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _series_opts(every=1, interp="c2", tail_tol=0.0):
+    return rsv_series_opts(int(every), _INTERP[interp] if isinstance(interp, str) else int(interp), float(tail_tol))
+
+
+def rsv_series_march(op: Operator, adjoint: bool, k: int, out, n_out_max: int, init=None, forcing=None,
+                     n_in: int = 0, reverse_in: bool = False, **opts):
+    """One series-driven run (device series [n][k][n_points]); returns (n_out, stops[k])."""
+    o = _series_opts(**opts)
+    n_out = ctypes.c_int64()
+    stops = np.zeros(k, dtype=np.int64)
+    _check(_lib.rsv_series_march(op.handle, int(bool(adjoint)), int(k), _ptr(init), _ptr(forcing), int(n_in),
+                                 int(bool(reverse_in)), ctypes.byref(o), _ptr(out), int(n_out_max),
+                                 ctypes.byref(n_out), stops.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return n_out.value, stops
+
+
+def rsv_series_fourier(op: Operator, series, n_snap: int, k: int, d: float, t0: float, omegas, out):
+    om, omp = _f64(omegas)
+    _check(_lib.rsv_series_fourier(op.handle, _ptr(series), int(n_snap), int(k), float(d), float(t0), omp,
+                                   len(om), _ptr(out)))
+
+
+def rsv_series_filter(op: Operator, x, n_in: int, k: int, taps, out, reverse_taps: bool = False):
+    """taps: complex [k][order + 1] (host)."""
+    t = np.ascontiguousarray(np.asarray(taps, dtype=np.complex128).reshape(k, -1))
+    _check(_lib.rsv_series_filter(op.handle, _ptr(x), int(n_in), int(k),
+                                  t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), t.shape[1] - 1,
+                                  int(bool(reverse_taps)), _ptr(out)))
+
+
+def rsv_fir_design(order: int, d: float, w_pts, amp) -> np.ndarray:
+    """Complex taps [order + 1] of the frequency-sampling design (host computation)."""
+    w, wp = _f64(w_pts)
+    a, ap = _f64(amp)
+    taps = np.zeros(order + 1, dtype=np.complex128)
+    _check(_lib.rsv_fir_design(int(order), float(d), wp, ap, len(w),
+                               taps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return taps
+
+
+def rsv_trm_power_iteration(op: Operator, f0, k: int, omegas, n_iter: int, n_snap_max: int, filter_order: int = 0,
+                            w_hat=None, **series_opts):
+    """TRM power iteration; returns the gain estimates [n_iter][n_omega][k] (host)."""
+    om, omp = _f64(omegas)
+    o = rsv_trm_opts(_series_opts(**series_opts), int(n_iter), int(filter_order), int(n_snap_max))
+    gains = np.zeros((n_iter, len(om), k))
+    _check(_lib.rsv_trm_power_iteration(op.handle, _ptr(f0), int(k), omp, len(om), ctypes.byref(o),
+                                        gains.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(w_hat)))
+    return gains
 
 
 PROFILE_CATEGORIES = ("synthesis", "march", "analysis", "glue")

@@ -53,7 +53,8 @@ def test_binding_covers_every_symbol(lib):
 def test_struct_layout_matches_header(tmp_path):
     from paper_2008_10904_gb300 import rsv
     import ctypes
-    fields = {"rsv_operator_desc": rsv.rsv_operator_desc, "rsv_march_opts": rsv.rsv_march_opts}
+    fields = {"rsv_operator_desc": rsv.rsv_operator_desc, "rsv_march_opts": rsv.rsv_march_opts,
+              "rsv_series_opts": rsv.rsv_series_opts, "rsv_trm_opts": rsv.rsv_trm_opts}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for sname, cls in fields.items():
         lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')
