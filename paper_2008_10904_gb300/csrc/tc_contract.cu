@@ -289,7 +289,7 @@ struct PipeBars {
   uint64_t raw_full[kRawRing], raw_empty[kRawRing];
   uint64_t a_full[kAStages], a_empty[kAStages];
   uint64_t b_full[kBRing], b_empty[kBRing];
-  uint64_t acc_full, acc_empty;
+  uint64_t acc_full[2], acc_empty[2];   // two tensor-memory accumulators of 256 columns
   int abort_flag;
 };
 
@@ -369,14 +369,17 @@ __device__ __forceinline__ void convert_row(const ContractArgs& a, int64_t r0, i
   }
 }
 
-// Columns [c0, c1) of row r: F stores, or FP64 accumulator read-modify-writes,
-// 32 columns per tensor-memory load, all loads of a group issued before use.
+// Accumulator columns [c0, c1) of row r (output columns coff + c): F stores, or FP64
+// accumulator read-modify-writes, 32 columns per tensor-memory load, all loads of a
+// group issued before use.
 template <int W>
-__device__ __forceinline__ void epilogue_cols(const ContractArgs& a, int64_t r, uint32_t tq, int c, bool row_ok) {
+__device__ __forceinline__ void epilogue_cols(const ContractArgs& a, int64_t r, uint32_t tq, int cl, int coff,
+                                              bool row_ok) {
   float v[32];
-  if (W == 32) tc::tmem_ld32(tq + (uint32_t)c, v);
-  else tc::tmem_ld16(tq + (uint32_t)c, v);
+  if (W == 32) tc::tmem_ld32(tq + (uint32_t)cl, v);
+  else tc::tmem_ld16(tq + (uint32_t)cl, v);
   if (!row_ok) return;
+  const int c = coff + cl;
   if (a.mode == SYNTH_C) {
     float2* F = reinterpret_cast<float2*>(a.out);
 #pragma unroll
@@ -409,11 +412,12 @@ __device__ __forceinline__ void epilogue_cols(const ContractArgs& a, int64_t r, 
   }
 }
 
-__device__ __forceinline__ void epilogue_tile(const ContractArgs& a, int64_t r, uint32_t tq, int c0, int c1) {
+__device__ __forceinline__ void epilogue_tile(const ContractArgs& a, int64_t r, uint32_t tq, int c0, int c1,
+                                              int coff) {
   const bool row_ok = r < a.rows;
   int c = c0;
-  for (; c + 32 <= c1; c += 32) epilogue_cols<32>(a, r, tq, c, row_ok);
-  if (c < c1) epilogue_cols<16>(a, r, tq, c, row_ok);
+  for (; c + 32 <= c1; c += 32) epilogue_cols<32>(a, r, tq, c, coff, row_ok);
+  if (c < c1) epilogue_cols<16>(a, r, tq, c, coff, row_ok);
 }
 
 __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(ContractArgs a) {
@@ -439,8 +443,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
       tc::mbar_init(&pb->b_full[i], 1);
       tc::mbar_init(&pb->b_empty[i], 1);
     }
-    tc::mbar_init(&pb->acc_full, 1);
-    tc::mbar_init(&pb->acc_empty, 256);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&pb->acc_full[i], 1);
+      tc::mbar_init(&pb->acc_empty[i], 256);
+    }
     pb->abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -451,7 +457,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
   const uint32_t tmem = tbase;
   const int chunks = a.K / kKc;
   const int64_t tiles = (a.rows + kRowsCta - 1) / kRowsCta;
-  const uint32_t bchunk_bytes = 4u * (uint32_t)a.N * kKc;
+  // Each row tile runs as one or two column sub-tiles of at most 256 columns; sub-tiles alternate
+  // between the two accumulators, so the products of one overlap the epilogue of the previous one.
+  const int nsub = a.N > 256 ? 2 : 1;
 
   if (warp == 12) {
     if (lane == 0) {  // producer of the long operand
@@ -460,10 +468,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
       for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
         const int64_t r0 = t * kRowsCta;
         const int nr = (int)min((int64_t)kRowsCta, a.rows - r0);
-        for (int kc = 0; kc < chunks; ++kc, ++g) {
-          const uint32_t rs = g % kRawRing, ru = g / kRawRing;
-          if (ru > 0 && !pwait(&pb->raw_empty[rs], (ru - 1) & 1, abort_flag)) { ok = false; break; }
-          issue_raw(a, r0, nr, kc, raw + rs * kRawBytes, &pb->raw_full[rs]);
+        for (int h = 0; h < nsub && ok; ++h) {   // the second sub-tile re-reads the rows from L2
+          for (int kc = 0; kc < chunks; ++kc, ++g) {
+            const uint32_t rs = g % kRawRing, ru = g / kRawRing;
+            if (ru > 0 && !pwait(&pb->raw_empty[rs], (ru - 1) & 1, abort_flag)) { ok = false; break; }
+            issue_raw(a, r0, nr, kc, raw + rs * kRawBytes, &pb->raw_full[rs]);
+          }
         }
       }
       if (!ok) {
@@ -479,14 +489,19 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
       uint32_t g = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        for (int kc = 0; kc < chunks; ++kc, ++g) {
-          const uint32_t bs = g % kBRing, bu = g / kBRing;
-          if (bu > 0 && !pwait(&pb->b_empty[bs], (bu - 1) & 1, abort_flag)) { ok = false; break; }
-          float* B_hi = sB + bs * 2 * kBStageFloats;
-          const float* bsrc = a.B + (size_t)kc * 2 * kBStageFloats;
-          tc::mbar_arrive_expect_tx(&pb->b_full[bs], 2 * bchunk_bytes);
-          tc::bulk_g2s(B_hi, bsrc, bchunk_bytes, &pb->b_full[bs]);
-          tc::bulk_g2s(B_hi + kBStageFloats, bsrc + kBStageFloats, bchunk_bytes, &pb->b_full[bs]);
+        for (int h = 0; h < nsub && ok; ++h) {
+          // rows [256 h, 256 h + nn) of a chunk are one contiguous run of 8-row core-matrix groups
+          const int nn = h == 0 ? min(256, a.N) : a.N - 256;
+          const uint32_t bytes = 4u * (uint32_t)nn * kKc;
+          for (int kc = 0; kc < chunks; ++kc, ++g) {
+            const uint32_t bs = g % kBRing, bu = g / kBRing;
+            if (bu > 0 && !pwait(&pb->b_empty[bs], (bu - 1) & 1, abort_flag)) { ok = false; break; }
+            float* B_hi = sB + bs * 2 * kBStageFloats;
+            const float* bsrc = a.B + (size_t)kc * 2 * kBStageFloats + (size_t)h * 256 * kKc;
+            tc::mbar_arrive_expect_tx(&pb->b_full[bs], 2 * bytes);
+            tc::bulk_g2s(B_hi, bsrc, bytes, &pb->b_full[bs]);
+            tc::bulk_g2s(B_hi + kBStageFloats, bsrc + kBStageFloats, bytes, &pb->b_full[bs]);
+          }
         }
       }
       if (!ok) {
@@ -502,47 +517,49 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
       uint32_t g = 0, tt = 0;
       bool ok = true;
       const uint32_t sbo = (kKc / 4) * 128;
-      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tt) {
-        if (tt > 0 && !pwait(&pb->acc_empty, (tt - 1) & 1, abort_flag)) { ok = false; break; }
-        tc::tc_fence_after();
-        for (int kc = 0; kc < chunks; ++kc, ++g) {
-          const uint32_t as = g % kAStages, au = g / kAStages;
-          const uint32_t bs = g % kBRing, bu = g / kBRing;
-          if (!pwait(&pb->a_full[as], au & 1, abort_flag) || !pwait(&pb->b_full[bs], bu & 1, abort_flag)) {
-            ok = false;
-            break;
-          }
+      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        for (int h = 0; h < nsub; ++h, ++tt) {
+          const uint32_t buf = tt & 1, use = tt >> 1;
+          if (use > 0 && !pwait(&pb->acc_empty[buf], (use - 1) & 1, abort_flag)) { ok = false; break; }
           tc::tc_fence_after();
-          const char* A_hi = reinterpret_cast<const char*>(sA + as * 2 * kAStageFloats);
-          const char* A_lo = A_hi + 4 * kAStageFloats;
-          const char* B_hi = reinterpret_cast<const char*>(sB + bs * 2 * kBStageFloats);
-          const char* B_lo = B_hi + 4 * kBStageFloats;
+          const int nn = h == 0 ? min(256, a.N) : a.N - 256;
+          const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)nn);
+          const uint32_t d = tmem + buf * 256u;
+          for (int kc = 0; kc < chunks; ++kc, ++g) {
+            const uint32_t as = g % kAStages, au = g / kAStages;
+            const uint32_t bs = g % kBRing, bu = g / kBRing;
+            if (!pwait(&pb->a_full[as], au & 1, abort_flag) || !pwait(&pb->b_full[bs], bu & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc::tc_fence_after();
+            const char* A_hi = reinterpret_cast<const char*>(sA + as * 2 * kAStageFloats);
+            const char* A_lo = A_hi + 4 * kAStageFloats;
+            const char* B_hi = reinterpret_cast<const char*>(sB + bs * 2 * kBStageFloats);
+            const char* B_lo = B_hi + 4 * kBStageFloats;
 #pragma unroll
-          for (int ks = 0; ks < kKc / 8; ++ks) {
-            const uint64_t ah = tc::smem_desc(A_hi + ks * 256, 128, sbo);
-            const uint64_t al = tc::smem_desc(A_lo + ks * 256, 128, sbo);
-            for (int nh = 0; nh < a.N; nh += 256) {
-              const int nn = min(256, a.N - nh);
-              const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)nn);
-              const uint64_t bh = tc::smem_desc(B_hi + ks * 256 + (nh / 8) * sbo, 128, sbo);
-              const uint64_t bl = tc::smem_desc(B_lo + ks * 256 + (nh / 8) * sbo, 128, sbo);
-              const uint32_t d = tmem + (uint32_t)nh;
+            for (int ks = 0; ks < kKc / 8; ++ks) {
+              const uint64_t ah = tc::smem_desc(A_hi + ks * 256, 128, sbo);
+              const uint64_t al = tc::smem_desc(A_lo + ks * 256, 128, sbo);
+              const uint64_t bh = tc::smem_desc(B_hi + ks * 256, 128, sbo);
+              const uint64_t bl = tc::smem_desc(B_lo + ks * 256, 128, sbo);
               tc::mma_tf32(d, ah, bh, idesc, kc > 0 || ks > 0);
               tc::mma_tf32(d, ah, bl, idesc, true);
               tc::mma_tf32(d, al, bh, idesc, true);
             }
+            tc::mma_commit(&pb->a_empty[as]);
+            tc::mma_commit(&pb->b_empty[bs]);
           }
-          tc::mma_commit(&pb->a_empty[as]);
-          tc::mma_commit(&pb->b_empty[bs]);
+          if (!ok) break;
+          tc::mma_commit(&pb->acc_full[buf]);
         }
-        if (!ok) break;
-        tc::mma_commit(&pb->acc_full);
       }
       if (!ok) {
         pabort(pb, a.err);
-        // every MMA issued so far completes before tensor memory is freed
-        tc::mma_commit(&pb->acc_full);
-        tc::mbar_wait(&pb->acc_full, tt & 1, kTries);
+        // every MMA issued so far completes before tensor memory is freed: a commit after them
+        // completes the next phase of the current sub-tile's accumulator barrier
+        tc::mma_commit(&pb->acc_full[tt & 1]);
+        tc::mbar_wait(&pb->acc_full[tt & 1], (tt >> 1) & 1, kTries);
       }
     }
   } else if (warp < 4) {  // converters: one row each
@@ -551,31 +568,38 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
     bool ok = true;
     for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
       const int64_t r0 = t * kRowsCta;
-      for (int kc = 0; kc < chunks; ++kc, ++g) {
-        const uint32_t rs = g % kRawRing, ru = g / kRawRing;
-        const uint32_t as = g % kAStages, au = g / kAStages;
-        if (!pwait(&pb->raw_full[rs], ru & 1, abort_flag)) { ok = false; break; }
-        if (au > 0 && !pwait(&pb->a_empty[as], (au - 1) & 1, abort_flag)) { ok = false; break; }
-        float* A_hi = sA + as * 2 * kAStageFloats;
-        convert_row(a, r0, kc, rr, raw + rs * kRawBytes, A_hi, A_hi + kAStageFloats);
-        tc::fence_proxy_async_smem();
-        mbar_arrive(&pb->a_full[as]);
-        mbar_arrive(&pb->raw_empty[rs]);
+      for (int h = 0; h < nsub && ok; ++h) {
+        for (int kc = 0; kc < chunks; ++kc, ++g) {
+          const uint32_t rs = g % kRawRing, ru = g / kRawRing;
+          const uint32_t as = g % kAStages, au = g / kAStages;
+          if (!pwait(&pb->raw_full[rs], ru & 1, abort_flag)) { ok = false; break; }
+          if (au > 0 && !pwait(&pb->a_empty[as], (au - 1) & 1, abort_flag)) { ok = false; break; }
+          float* A_hi = sA + as * 2 * kAStageFloats;
+          convert_row(a, r0, kc, rr, raw + rs * kRawBytes, A_hi, A_hi + kAStageFloats);
+          tc::fence_proxy_async_smem();
+          mbar_arrive(&pb->a_full[as]);
+          mbar_arrive(&pb->raw_empty[rs]);
+        }
       }
     }
     if (!ok) pabort(pb, a.err);
   } else if (warp >= 4 && warp < 12) {  // epilogue: TMEM lane quadrant warp % 4, one half of the columns
     const int q = warp & 3;
-    const int half = round16c((a.N + 1) / 2);
-    const int c0 = warp < 8 ? 0 : half, c1 = warp < 8 ? half : a.N;
     uint32_t tt = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tt) {
-      if (!pwait(&pb->acc_full, tt & 1, abort_flag)) { ok = false; break; }
-      tc::tc_fence_after();
-      epilogue_tile(a, t * kRowsCta + 32 * q + lane, tmem + ((uint32_t)(32 * q) << 16), c0, c1);
-      tc::tc_fence_before();
-      mbar_arrive(&pb->acc_empty);
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      for (int h = 0; h < nsub; ++h, ++tt) {
+        const uint32_t buf = tt & 1;
+        if (!pwait(&pb->acc_full[buf], (tt >> 1) & 1, abort_flag)) { ok = false; break; }
+        tc::tc_fence_after();
+        const int nn = h == 0 ? min(256, a.N) : a.N - 256;
+        const int half = round16c((nn + 1) / 2);
+        const int c0 = warp < 8 ? 0 : half, c1 = warp < 8 ? half : nn;
+        epilogue_tile(a, t * kRowsCta + 32 * q + lane, tmem + ((uint32_t)(32 * q) << 16) + buf * 256u, c0, c1,
+                      256 * h);
+        tc::tc_fence_before();
+        mbar_arrive(&pb->acc_empty[buf]);
+      }
     }
     if (!ok) pabort(pb, a.err);
   }
@@ -662,12 +686,12 @@ cudaError_t run(ContractArgs& a, const TileGeom& g, rsv_operator op) {
   const int64_t total = (int64_t)kMaxN * a.K;
   build_b_kernel<<<(unsigned)((total + 255) / 256), 256, 0, op->stream>>>(a, g, (const cpx<float>*)op->d_tw, op->d_pj,
                                                                           op->d_cw, (float*)op->ws_tcb.ptr);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(tc_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    cudaFuncSetAttribute(tc_contract_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeSmem);
-    attr_set = true;
-  }
+  // the shared-memory opt-in is a per-device attribute: set it before every launch (cheap next
+  // to a launch that moves gigabytes), so that any device and any thread gets it
+  cudaError_t ae = cudaFuncSetAttribute(tc_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (ae == cudaSuccess)
+    ae = cudaFuncSetAttribute(tc_contract_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeSmem);
+  if (ae != cudaSuccess) return ae;
   const int64_t tiles = (a.rows + kRowsCta - 1) / kRowsCta;
   if (pipe_ok(a, op)) {
     const unsigned blocks = (unsigned)std::min<int64_t>(tiles, (int64_t)op->sm_count);
