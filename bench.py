@@ -529,6 +529,12 @@ def run_ours(args):
         rsv.rsv_orthonormalize(op, dst, w.k, rfac if read_r else None)
         counter[0] += 1
 
+    # measured tile length and vector group (untimed): one timed tile per candidate configuration
+    tuned = None
+    if args.tile == 0 and not args.no_autotune:
+        t_s, t_g = rsv.rsv_autotune(op, bufs[0], w.k, **opts)
+        tuned = {"tile": t_s, "group": t_g, "chosen_by": "rsv_autotune: one timed tile per candidate "
+                 "(default tile and half of it x groups of k, k/2, k/4, 1 that fit), least time per vector-step"}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -605,7 +611,8 @@ def run_ours(args):
                    "actions_per_step": actions_per_step(w, step_kind),
                    "power_iterations": w.n_power_iter, "precision": prec_name,
                    "l2": "flushed between steps (512 MiB write outside the timed events); state blocks exceed L2",
-                   "parallelism": f"independent replicas x{ws}", "path": path},
+                   "parallelism": f"independent replicas x{ws}", "path": path,
+                   "tiles": tuned or {"chosen_by": "memory rule" if args.tile == 0 else f"--tile {args.tile}"}},
         "e2e": {"value": e2e_value, "unit": "actions/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "gpu_launches": launches,
@@ -658,6 +665,7 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default=None,
                     help="bf16: the 3-D workload's march state stored in BF16 (arithmetic in FP32)")
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the memory rule's tile and group")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement (<= --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")

@@ -317,6 +317,19 @@ rsv_status rsv_orthonormalize(rsv_operator op, void* block, int32_t k, double* r
  * act on real and imaginary parts alike).  For testing the operator kernels. */
 rsv_status rsv_apply_operator(rsv_operator op, const void* x, int32_t k, int32_t adjoint, void* y);
 
+/* Measured choice of the march's time-tile length and vector-group size for
+ * marches of k vectors with these options.  Candidates: the default tile and
+ * half of it, times groups of k, k/2, k/4 and 1 vectors that fit in device
+ * memory next to what is allocated; each is timed on one synthesised, marched
+ * and analysed tile of the first vector group of f_hat (device [n_omega][k][n],
+ * the block a following march will use; nothing is written to it), and the
+ * configuration with the least time per vector-step is kept in the operator
+ * for later marches of k vectors whose opts->tile_steps is 0.  tile, group:
+ * host (nullable), the chosen values.  Errors: INVALID_ARG, STATE, OOM (no
+ * candidate fits), and those of the march. */
+rsv_status rsv_autotune(rsv_operator op, const void* f_hat, int32_t k, const rsv_march_opts* opts, int32_t* tile,
+                        int32_t* group);
+
 /* ---------------------------------------------------------------------------
  * Transient-response method in time-series form (Sec. 2.2 with App. B and C).
  *

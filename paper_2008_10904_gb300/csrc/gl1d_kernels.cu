@@ -291,6 +291,141 @@ __global__ void __launch_bounds__(MAXT) gl1d_cn_tile_kernel(Gl1dTile t, cpx<R>* 
   }
 }
 
+// Packed RK4 tile kernel for batches of uneven instances: one CTA of PPT x blockDim slots holds
+// several (instance, vector) segments back to back, each followed by a zero slot, so the three-point
+// stencil of a segment's end points reads zeros exactly as at an instance's Dirichlet ends.
+// map[pack][slot] is the row (vector * n + point) of the slot's point, or -1 for a separator or an
+// unused slot.  The steps, the stage exchange and the forcing prefetch are those of
+// gl1d_tile_kernel; the divergence flag is raised per point (the march reads norms elsewhere).
+template <typename R, int PPT>
+__global__ void __launch_bounds__(1024) gl1d_pack_kernel(Gl1dTile t, const int32_t* __restrict__ map,
+                                                         cpx<R>* __restrict__ u, const cpx<R>* __restrict__ F,
+                                                         cpx<R>* __restrict__ Y, int* __restrict__ flag) {
+  extern __shared__ unsigned char smem_raw[];
+  const int cap = PPT * (int)blockDim.x;
+  const int ld = cap + 2;
+  cpx<R>* sx = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][cap + 2]: zero halo, slots 1..cap, zero
+  const cpx<R>* lo = reinterpret_cast<const cpx<R>*>(t.lo);
+  const cpx<R>* di = reinterpret_cast<const cpx<R>*>(t.di);
+  const cpx<R>* up = reinterpret_cast<const cpx<R>*>(t.up);
+  const cpx<R> zero = mk<R>(0, 0);
+  for (int i = threadIdx.x; i < 2 * ld; i += blockDim.x) sx[i] = zero;   // separators stay zero
+  const int64_t rows = (int64_t)t.kg * t.n;
+  const int32_t* pm = map + (int64_t)blockIdx.x * cap;
+  int64_t row[PPT];
+  cpx<R> cl[PPT], cd[PPT], cu[PPT], us[PPT];
+  bool ok[PPT];
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) {
+    const int i = threadIdx.x + m * blockDim.x;
+    const int32_t r = pm[i];
+    ok[m] = r >= 0;
+    row[m] = r;
+    if (ok[m]) {
+      const int64_t p = r % t.n;
+      cl[m] = lo[p];
+      cd[m] = di[p];
+      cu[m] = up[p];
+      us[m] = u[r];
+    } else {
+      cl[m] = cd[m] = cu[m] = us[m] = zero;
+    }
+  }
+  __syncthreads();
+  const R h = R(t.h);
+  const R h2 = R(0.5) * h;
+  const R h6 = h / R(6);
+  int buf = 0;
+  auto stage = [&](const cpx<R>* x, const cpx<R>* f, cpx<R>* y) {
+    cpx<R>* s = sx + buf * ld;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m)
+      if (ok[m]) s[1 + threadIdx.x + m * blockDim.x] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      const int i = threadIdx.x + m * blockDim.x;
+      cpx<R> a = f[m];
+      if (ok[m]) {
+        cfma(a, cl[m], s[i]);
+        cfma(a, cd[m], x[m]);
+        cfma(a, cu[m], s[i + 2]);
+      }
+      y[m] = a;
+    }
+    buf ^= 1;
+  };
+  auto load_f = [&](int s, cpx<R>* fh_out, cpx<R>* f1_out) {
+    const bool forced = (F != nullptr) && (t.n0 + s < t.n_forced);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      fh_out[m] = f1_out[m] = zero;
+      if (forced && ok[m]) {
+        fh_out[m] = F[(int64_t)(2 * s + 1) * rows + row[m]];
+        f1_out[m] = F[(int64_t)(2 * s + 2) * rows + row[m]];
+      }
+    }
+  };
+  cpx<R> f0[PPT], fh[PPT], f1[PPT], nfh[PPT], nf1[PPT];
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) f0[m] = nfh[m] = nf1[m] = zero;
+  if (F != nullptr && t.n0 < t.n_forced) {
+#pragma unroll
+    for (int m = 0; m < PPT; ++m)
+      if (ok[m]) f0[m] = F[row[m]];
+  }
+  load_f(0, fh, f1);
+  for (int s = 0; s < t.steps; ++s) {
+    if (s + 1 < t.steps) load_f(s + 1, nfh, nf1);
+    if (!((F != nullptr) && (t.n0 + s < t.n_forced))) {
+#pragma unroll
+      for (int m = 0; m < PPT; ++m) f0[m] = zero;
+    }
+    if (Y != nullptr && s >= t.y_first) {
+#pragma unroll
+      for (int m = 0; m < PPT; ++m)
+        if (ok[m]) Y[(int64_t)s * rows + row[m]] = us[m];
+    }
+    cpx<R> k[PPT], x[PPT], acc[PPT];
+    stage(us, f0, k);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      acc[m] = k[m];
+      x[m] = us[m] + h2 * k[m];
+    }
+    stage(x, fh, k);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      acc[m] = acc[m] + R(2) * k[m];
+      x[m] = us[m] + h2 * k[m];
+    }
+    stage(x, fh, k);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      acc[m] = acc[m] + R(2) * k[m];
+      x[m] = us[m] + h * k[m];
+    }
+    stage(x, f1, k);
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      us[m] = us[m] + h6 * (acc[m] + k[m]);
+      f0[m] = f1[m];
+      fh[m] = nfh[m];
+      f1[m] = nf1[m];
+    }
+  }
+  bool bad = false;
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) {
+    if (ok[m]) {
+      u[row[m]] = us[m];
+      const double q = (double)us[m].re * (double)us[m].re + (double)us[m].im * (double)us[m].im;
+      bad = bad || !(q < 1e300);
+    }
+  }
+  if (bad) atomicExch(flag, 1);   // NaN or overflow
+}
+
 template <typename R>
 __global__ void gl1d_apply_kernel(Gl1dTile t, const cpx<R>* __restrict__ x, cpx<R>* __restrict__ y,
                                   const int32_t* __restrict__ inst_of_point) {
@@ -344,6 +479,27 @@ cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y,
   return launch_ppt<R, 4, 1024>(t, threads, u, F, Y, norms, flag, st);
 }
 
+// Packed launch: n_packs CTAs of 1024 threads, ppt slots per thread (map from build_gl1d_packs).
+template <typename R>
+cudaError_t launch_gl1d_pack(const Gl1dTile& t, const int32_t* map, int n_packs, int ppt, void* u, const void* F,
+                             void* Y, int* flag, cudaStream_t st) {
+  const int threads = 1024;
+  const size_t smem = sizeof(cpx<R>) * 2 * (size_t)(ppt * threads + 2);
+  auto go = [&](auto kernel) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kernel<<<(unsigned)n_packs, threads, smem, st>>>(t, map, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y, flag);
+    return cudaGetLastError();
+  };
+  if (ppt == 1) return go(gl1d_pack_kernel<R, 1>);
+  if (ppt == 2) return go(gl1d_pack_kernel<R, 2>);
+  if (ppt == 3) return go(gl1d_pack_kernel<R, 3>);
+  if (ppt == 4) return go(gl1d_pack_kernel<R, 4>);
+  return cudaErrorInvalidValue;
+}
+
 template <typename R>
 cudaError_t launch_gl1d_apply(const Gl1dTile& t, const int32_t* inst_of_point, const void* x, void* y,
                               cudaStream_t st) {
@@ -356,6 +512,10 @@ template cudaError_t launch_gl1d_tile<double>(const Gl1dTile&, void*, const void
                                              cudaStream_t);
 template cudaError_t launch_gl1d_tile<float>(const Gl1dTile&, void*, const void*, void*, double*, int*,
                                             cudaStream_t);
+template cudaError_t launch_gl1d_pack<double>(const Gl1dTile&, const int32_t*, int, int, void*, const void*, void*,
+                                             int*, cudaStream_t);
+template cudaError_t launch_gl1d_pack<float>(const Gl1dTile&, const int32_t*, int, int, void*, const void*, void*,
+                                            int*, cudaStream_t);
 template cudaError_t launch_gl1d_apply<double>(const Gl1dTile&, const int32_t*, const void*, void*, cudaStream_t);
 template cudaError_t launch_gl1d_apply<float>(const Gl1dTile&, const int32_t*, const void*, void*, cudaStream_t);
 

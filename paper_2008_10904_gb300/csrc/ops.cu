@@ -399,8 +399,88 @@ static Gl1dTile gl1d_geom(rsv_operator op, bool adjoint, int kg) {
   return g;
 }
 
+// Packing of uneven GL1D batches: when the one-CTA-per-(instance, vector) launch needs more CTAs than
+// there are SMs, the (instance, vector) segments are packed first-fit-decreasing into CTAs of 1024
+// threads x ppt slots (each segment followed by a zero separator slot), so that short instances do
+// not hold a CTA sized for the longest one.  RSV_GL1D_PACK=0 keeps the one-per-pair launch.
+static bool gl1d_pack_wanted(rsv_operator op, int kg) {
+  static const bool env = [] {
+    const char* e = getenv("RSV_GL1D_PACK");
+    return !(e != nullptr && e[0] == '0');
+  }();
+  return env && op->scheme == RSV_SCHEME_RK4 && op->n_inst > 1 && op->gl_max_n <= 4096 &&
+         (int64_t)op->n_inst * kg > op->sm_count && (int64_t)kg * op->n < ((int64_t)1 << 31);
+}
+
+namespace {
+struct PackItem {
+  int64_t len;
+  int inst, v;
+};
+// First-fit decreasing of the (instance, vector) segments into packs of cap slots.
+std::vector<std::vector<PackItem>> pack_items(const std::vector<PackItem>& items, int64_t cap) {
+  std::vector<int64_t> used;                 // slots used per pack (separators included)
+  std::vector<std::vector<PackItem>> packs;
+  for (const PackItem& it : items) {
+    size_t b = 0;
+    for (; b < packs.size(); ++b)
+      if (used[b] + (used[b] > 0 ? 1 : 0) + it.len <= cap) break;
+    if (b == packs.size()) {
+      packs.emplace_back();
+      used.push_back(0);
+    }
+    used[b] += (used[b] > 0 ? 1 : 0) + it.len;
+    packs[b].push_back(it);
+  }
+  return packs;
+}
+}  // namespace
+
+// Slots per thread: the fewest that hold the longest instance.  More slots per thread (fewer CTAs,
+// down to one wave of one 1024-thread CTA per SM) measured slower on the 64-instance batch (3 slots:
+// 679 ms against 581 ms for 2 slots in two waves; the kernel is bound by per-SM issue and barrier
+// latency, not by the number of waves), so they are used only when RSV_GL1D_PPT forces them.
+static cudaError_t gl1d_build_packs(rsv_operator op, int kg) {
+  if (op->pack_map != nullptr && op->pack_kg == kg) return cudaSuccess;
+  std::vector<PackItem> items;
+  for (int v = 0; v < kg; ++v)
+    for (int i = 0; i < op->n_inst; ++i) items.push_back({op->inst_len[i], i, v});
+  std::stable_sort(items.begin(), items.end(), [](const PackItem& a, const PackItem& b) { return a.len > b.len; });
+  int ppt = (int)((op->gl_max_n + 1023) / 1024);
+  std::vector<std::vector<PackItem>> packs = pack_items(items, 1024 * (int64_t)ppt);
+  const char* env = getenv("RSV_GL1D_PPT");
+  const int forced = env ? atoi(env) : 0;
+  if (forced >= ppt && forced <= 4) {
+    ppt = forced;
+    packs = pack_items(items, 1024 * (int64_t)ppt);
+  }
+  const int cap = 1024 * ppt;
+  std::vector<int32_t> map(packs.size() * (size_t)cap, -1);
+  for (size_t b = 0; b < packs.size(); ++b) {
+    int64_t pos = 0;
+    for (const PackItem& it : packs[b]) {
+      const int64_t r0 = (int64_t)it.v * op->n + op->inst_off[it.inst];
+      for (int64_t j = 0; j < it.len; ++j) map[b * cap + pos + j] = (int32_t)(r0 + j);
+      pos += it.len + 1;
+    }
+  }
+  if (op->pack_map) cudaFree(op->pack_map);
+  op->pack_map = nullptr;
+  op->pack_kg = 0;
+  cudaError_t e = cudaMalloc(&op->pack_map, map.size() * sizeof(int32_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(op->pack_map, map.data(), map.size() * sizeof(int32_t), cudaMemcpyHostToDevice, op->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(op->stream);
+  if (e != cudaSuccess) return e;
+  op->pack_kg = kg;
+  op->pack_count = (int)packs.size();
+  op->pack_ppt = ppt;
+  return cudaSuccess;
+}
+
 template <typename R>
-cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const void* F, void* Y, double* norms) {
+static cudaError_t march_tile_direct(rsv_operator op, const MarchTile& t, void* state, const void* F, void* Y,
+                                     double* norms) {
   switch (op->kind) {
     case RSV_OP_GL1D: {
       Gl1dTile g = gl1d_geom(op, t.adjoint, t.kg);
@@ -408,6 +488,12 @@ cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const v
       g.steps = t.steps;
       g.n_forced = t.n_forced;
       g.y_first = t.y_first;
+      if (gl1d_pack_wanted(op, t.kg)) {
+        cudaError_t e = gl1d_build_packs(op, t.kg);
+        if (e != cudaSuccess) return e;
+        return launch_gl1d_pack<R>(g, (const int32_t*)op->pack_map, op->pack_count, op->pack_ppt, state, F, Y,
+                                   op->d_flag, op->stream);
+      }
       return launch_gl1d_tile<R>(g, state, F, Y, norms, op->d_flag, op->stream);
     }
     case RSV_OP_DENSE: {
@@ -441,6 +527,73 @@ cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const v
     default:
       return cudaErrorNotSupported;
   }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs of a time tile's launch sequence (structured-grid kinds: two to four launches per
+// step).  What a tile launches depends on the tile only through tile-relative quantities: the step
+// count, how many of its steps are forced, which steps store snapshots, the vector group and the
+// workspace pointers.  So the tile is described relative to its first step (n0 = 0, n_forced = the
+// forced steps of the tile), and a sequence met a second time is captured once into a graph on a
+// private stream and replayed on the operator's stream from then on.  The first meeting runs the
+// launches directly (one-time set-up such as shared-memory opt-ins stays outside any capture).  A
+// capture that fails falls back to direct launches for that sequence.  RSV_TILE_GRAPHS=0 disables.
+// ---------------------------------------------------------------------------
+static bool tile_graphs_enabled(rsv_operator op) {
+  static const bool env = [] {
+    const char* e = getenv("RSV_TILE_GRAPHS");
+    return !(e != nullptr && e[0] == '0');
+  }();
+  return env && (op->kind == RSV_OP_ADR2D || op->kind == RSV_OP_ADV3D);
+}
+
+template <typename R>
+cudaError_t march_tile(rsv_operator op, const MarchTile& t, void* state, const void* F, void* Y, double* norms) {
+  if (!tile_graphs_enabled(op)) return march_tile_direct<R>(op, t, state, F, Y, norms);
+  MarchTile rel = t;
+  rel.n0 = 0;
+  rel.n_forced = F != nullptr ? std::max<int64_t>(0, std::min<int64_t>(t.steps, t.n_forced - t.n0)) : 0;
+  const void* Fk = rel.n_forced > 0 ? F : nullptr;
+  TileGraphKey key{sizeof(R), rel.steps, (int)rel.n_forced, Y != nullptr ? rel.y_first : -1, rel.kg,
+                   rel.adjoint, state, Fk, Y, norms};
+  TileGraph* hit = nullptr;
+  for (TileGraph& g : op->tile_graphs)
+    if (g.key == key) hit = &g;
+  if (hit == nullptr) {
+    if (op->tile_graphs.size() >= 8) {   // bounded cache: drop the oldest sequence
+      if (op->tile_graphs.front().exec) cudaGraphExecDestroy(op->tile_graphs.front().exec);
+      op->tile_graphs.erase(op->tile_graphs.begin());
+    }
+    op->tile_graphs.push_back(TileGraph{key, nullptr, 1, false});
+    return march_tile_direct<R>(op, rel, state, Fk, Y, norms);
+  }
+  if (hit->exec == nullptr && !hit->failed) {
+    if (op->cap_stream == nullptr && cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      hit->failed = true;
+    } else {
+      const cudaStream_t orig = op->stream;
+      op->stream = op->cap_stream;
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(op->cap_stream, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        const cudaError_t el = march_tile_direct<R>(op, rel, state, Fk, Y, norms);
+        e = cudaStreamEndCapture(op->cap_stream, &graph);
+        if (e == cudaSuccess) e = el;
+      }
+      op->stream = orig;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&hit->exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        hit->exec = nullptr;
+        hit->failed = true;
+      }
+    }
+  }
+  if (hit->exec == nullptr) return march_tile_direct<R>(op, rel, state, Fk, Y, norms);
+  op->graph_replays += 1;
+  return cudaGraphLaunch(hit->exec, op->stream);
 }
 
 template <typename R>

@@ -126,6 +126,10 @@ rsv_operator_s::~rsv_operator_s() {
   if (d_flag) cudaFree(d_flag);
   if (d_wt) cudaFree(d_wt);
   if (pcr) cudaFree(pcr);
+  if (pack_map) cudaFree(pack_map);
+  for (rsv::TileGraph& g : tile_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
   if (ws_scaled.ptr) cudaFree(ws_scaled.ptr);
   for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
 }
@@ -261,13 +265,18 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
       path = "cuda-core propagator step";
   }
   const char* contract = (op->prec == RSV_PREC_FP32 && !op->tc_contract_disabled) ? "tcgen05" : "cuda-core";
+  char packs[64] = "";
+  if (op->kind == RSV_OP_GL1D && op->pack_kg > 0)
+    snprintf(packs, sizeof(packs), " packed=%d ctas of %d slots", op->pack_count, 1024 * op->pack_ppt);
+  char tuned[64] = "";
+  if (op->tuned_k > 0) snprintf(tuned, sizeof(tuned), " tuned=%d/%d for k=%d", op->tuned_tile, op->tuned_group, op->tuned_k);
   snprintf(buf, (size_t)buflen,
-           "kind=%s precision=%s n=%lld instances=%d path=%s contractions=%s resident_ctas=%d sms=%d tile=%d "
-           "group=%d steps=%lld",
+           "kind=%s precision=%s n=%lld instances=%d path=%s%s contractions=%s resident_ctas=%d sms=%d tile=%d "
+           "group=%d steps=%lld graphs=%d%s",
            (op->kind >= 0 && op->kind < 4) ? kinds[op->kind] : "?",
            op->prec == RSV_PREC_FP64 ? "fp64" : (op->bf16_state ? "bf16-state" : "fp32"),
-           (long long)op->n, op->n_inst, path, contract, op->tc_max_clusters, op->sm_count, op->last_tile,
-           op->last_group, (long long)op->last_steps);
+           (long long)op->n, op->n_inst, path, packs, contract, op->tc_max_clusters, op->sm_count, op->last_tile,
+           op->last_group, (long long)op->last_steps, (int)op->graph_replays, tuned);
   return RSV_OK;
 }
 
@@ -533,9 +542,18 @@ static void march_scalings(rsv_operator op, int scaling, bool adjoint, const dou
   }
 }
 
+// A timed trial of one tile configuration for rsv_autotune: the first vector group of kg vectors,
+// one forced and analysed time tile of S steps, accumulators in the workspace, nothing written to
+// the caller; *ms receives the device time of the tile's launches.
+struct TileTrial {
+  int S, kg;
+  float* ms;
+  int* steps;   // steps of the timed tile
+};
+
 template <typename R>
 static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out,
-                             bool adjoint, int scaling) {
+                             bool adjoint, int scaling, const TileTrial* trial = nullptr) {
   const double *s_in = nullptr, *s_out = nullptr;
   march_scalings(op, scaling, adjoint, &s_in, &s_out);
   Schedule sc;
@@ -546,8 +564,13 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
   // Tile length S and vector-group size kg: the requested / default tile and all k vectors, shrunk
   // (kg halved, then S down to 16) until the march workspace fits in 90% of the device memory not
   // held by others.
-  int S = (opts && opts->tile_steps > 0) ? opts->tile_steps : default_tile_steps(op);
-  int kg = k;
+  int S = (opts && opts->tile_steps > 0) ? opts->tile_steps
+                                         : (op->tuned_k == k ? op->tuned_tile : default_tile_steps(op));
+  int kg = (op->tuned_k == k && !(opts && opts->tile_steps > 0)) ? op->tuned_group : k;
+  if (trial) {
+    S = trial->S;
+    kg = trial->kg;
+  }
   {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -567,6 +590,7 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
     };
     // per-tile traffic (coefficients, FP64 accumulators) is amortised over S, while the vector
     // group only sets how much is resident: shrink the group first, then the tile
+    if (trial && need(S, kg) > budget) return fail(RSV_ERR_OOM, "trial configuration does not fit");
     while (need(S, kg) > budget && (S > 16 || kg > 1)) {
       if (kg > 1)
         kg = (kg + 1) / 2;
@@ -583,12 +607,26 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
   if ((st = ensure(op->ws_ftile, (size_t)(2 * S + 1) * rows_max * se)) != RSV_OK) return st;
   if ((st = ensure(op->ws_ysnap, (size_t)S * rows_max * se)) != RSV_OK) return st;
   if ((st = ensure(op->ws_norm, (size_t)kg * op->n_inst * sizeof(double))) != RSV_OK) return st;
-  const bool acc_in_out = (op->prec == RSV_PREC_FP64);
+  const bool acc_in_out = (op->prec == RSV_PREC_FP64) && trial == nullptr;
   if (!acc_in_out && (st = ensure(op->ws_acc, (size_t)op->n_omega * rows_max * sizeof(cpx<double>))) != RSV_OK)
     return st;
   if ((e = cudaMemsetAsync(op->d_flag, 0, sizeof(int), stream)) != cudaSuccess) return cuda_fail(e, "flag reset");
   const size_t ce = coef_bytes(op);
-  for (int v0 = 0; v0 < k; v0 += kg) {
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (trial) {
+    if ((e = cudaEventCreate(&ev0)) != cudaSuccess || (e = cudaEventCreate(&ev1)) != cudaSuccess) {
+      if (ev0) cudaEventDestroy(ev0);
+      return cuda_fail(e, "trial events");
+    }
+  }
+  struct EventGuard {
+    cudaEvent_t a, b;
+    ~EventGuard() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev_guard{ev0, ev1};
+  for (int v0 = 0; v0 < (trial ? std::min(kg, k) : k); v0 += kg) {
     const int kv = std::min(kg, k - v0);
     const int64_t rows = (int64_t)kv * n;
     cpx<double>* acc;
@@ -632,12 +670,13 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
     // TRM truncation by the state norm: per-vector peak over the tile ends so far
     const bool truncate = opts != nullptr && opts->variant == RSV_TRM && opts->tail_tol > 0.0;
     std::vector<double> peak(truncate ? kv : 0, 0.0), nrm(truncate ? kv : 0, 0.0);
-    for (int64_t n0 = 0; n0 < sc.total; n0 += S) {
+    if (trial && (e = cudaEventRecord(ev0, stream)) != cudaSuccess) return cuda_fail(e, "trial event");
+    for (int64_t n0 = 0; n0 < (trial ? std::min<int64_t>(S, sc.total) : sc.total); n0 += S) {
       g.n0 = n0;
       g.steps = (int)std::min<int64_t>(S, sc.total - n0);
       g.n_tau = synth_stride == 2 ? g.steps : 0;
-      const bool forced = n0 < sc.forced;
-      const bool analysed = n0 + g.steps > sc.first;
+      const bool forced = trial ? true : n0 < sc.forced;
+      const bool analysed = trial ? true : n0 + g.steps > sc.first;
       if (forced) {
         if (sizeof(R) == 4 && tc_contract_supported(op, true)) {
           const int nt = g.n_tau > 0 ? g.n_tau : 2 * g.steps + 1;
@@ -650,11 +689,11 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
         }
         if (e != cudaSuccess) return cuda_fail(e, "synthesis");
       }
-      const int y_first = analysed ? (int)std::max<int64_t>(0, sc.first - n0) : g.steps;
+      const int y_first = trial ? 0 : (analysed ? (int)std::max<int64_t>(0, sc.first - n0) : g.steps);
       MarchTile mt;
       mt.n0 = n0;
       mt.steps = g.steps;
-      mt.n_forced = sc.forced;
+      mt.n_forced = trial ? n0 + g.steps : sc.forced;
       mt.y_first = y_first;
       mt.kg = kv;
       mt.adjoint = adjoint;
@@ -692,6 +731,16 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
         if (n_end >= sc.forced && small) break;
       }
     }
+    if (trial) {
+      float ms = 0.f;
+      e = cudaEventRecord(ev1, stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+      if (e != cudaSuccess) return cuda_fail(e, "trial timing");
+      *trial->ms = ms;
+      *trial->steps = g.steps;
+      break;
+    }
     if (!truncate) op->last_steps = sc.total;
     void* o = static_cast<char*>(out) + (size_t)v0 * n * ce;
     e = launch_finish<R>(acc, acc_stride, op->n_omega, rows, 1.0 / (double)op->n_t, o, (int64_t)k * n, stream,
@@ -704,6 +753,46 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
   if (e != cudaSuccess) return cuda_fail(e, "march");
   if (flag == 2) return fail(RSV_ERR_TIMEOUT, "a bounded device wait expired in the tensor-core step");
   if (flag) return fail(RSV_ERR_DIVERGED, "state norm became non-finite during the march");
+  return RSV_OK;
+}
+
+// Measured choice of the tile length and vector group (rsv_autotune): candidates S in {D, D/2}
+// (D the default tile) and kg in {k, k/2, k/4, 1}, each timed on one forced and analysed tile of
+// the first vector group (run twice, the second timing kept), compared by time per vector-step.
+template <typename R>
+static rsv_status autotune_impl(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, int32_t* tile,
+                                int32_t* group) {
+  const int d = default_tile_steps(op);
+  std::vector<int> ss = {d};
+  if (d / 2 >= 16) ss.push_back(d / 2);
+  std::vector<int> gs;
+  for (int c : {k, (k + 1) / 2, (k + 3) / 4, 1})
+    if (std::find(gs.begin(), gs.end(), c) == gs.end()) gs.push_back(c);
+  double best = 1e300;
+  int bs = 0, bg = 0;
+  for (int S : ss)
+    for (int kg : gs) {
+      float ms = 0.f;
+      int steps = 0;
+      TileTrial tr{S, kg, &ms, &steps};
+      rsv_status st = RSV_OK;
+      for (int rep = 0; rep < 2 && st == RSV_OK; ++rep)
+        st = march_impl<R>(op, in, k, opts, nullptr, false, SCALE_NONE, &tr);
+      if (st == RSV_ERR_OOM) continue;   // does not fit next to the caller's blocks
+      if (st != RSV_OK) return st;
+      const double per = (double)ms / ((double)std::max(steps, 1) * std::min(kg, k));
+      if (per < best) {
+        best = per;
+        bs = S;
+        bg = kg;
+      }
+    }
+  if (bs == 0) return fail(RSV_ERR_OOM, "no tile configuration fits in device memory");
+  op->tuned_k = k;
+  op->tuned_tile = bs;
+  op->tuned_group = bg;
+  if (tile) *tile = bs;
+  if (group) *group = bg;
   return RSV_OK;
 }
 
@@ -729,6 +818,14 @@ extern "C" rsv_status rsv_march_adjoint(rsv_operator op, const void* y_hat, int3
 }
 
 // Diagonal B, C, W_f, W_y (Sec. 2.1).  The per-point factors the runs use are formed here in FP64.
+extern "C" rsv_status rsv_autotune(rsv_operator op, const void* f_hat, int32_t k, const rsv_march_opts* opts,
+                                   int32_t* tile, int32_t* group) {
+  if (!op || !f_hat || k < 1) return fail(RSV_ERR_INVALID_ARG, "bad autotune arguments");
+  if (!op->have_freq) return fail(RSV_ERR_STATE, "rsv_set_frequencies must come first");
+  return op->prec == RSV_PREC_FP64 ? autotune_impl<double>(op, f_hat, k, opts, tile, group)
+                                   : autotune_impl<float>(op, f_hat, k, opts, tile, group);
+}
+
 extern "C" rsv_status rsv_set_weights(rsv_operator op, const double* b, const double* c, const double* w_f,
                                       const double* w_y) {
   if (!op) return fail(RSV_ERR_INVALID_ARG, "null operator");

@@ -89,6 +89,26 @@ struct Profiler {
 
 }  // namespace rsv
 
+namespace rsv {
+// Launch sequence of one time tile, relative to its first step (ops.cu, CUDA graphs).
+struct TileGraphKey {
+  size_t elem;
+  int steps, forced, y_first, kg;
+  bool adjoint;
+  const void *state, *F, *Y, *norms;
+  bool operator==(const TileGraphKey& o) const {
+    return elem == o.elem && steps == o.steps && forced == o.forced && y_first == o.y_first && kg == o.kg &&
+           adjoint == o.adjoint && state == o.state && F == o.F && Y == o.Y && norms == o.norms;
+  }
+};
+struct TileGraph {
+  TileGraphKey key;
+  cudaGraphExec_t exec;
+  int seen;
+  bool failed;
+};
+}  // namespace rsv
+
 struct rsv_operator_s {
   int kind = 0;
   int prec = 0;                          // RSV_PREC_FP64 or RSV_PREC_FP32 (also for BF16 state)
@@ -119,6 +139,9 @@ struct rsv_operator_s {
   // GL1D: tridiagonal coefficients, direct then adjoint: lo, di, up
   void* tri[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int gl_max_n = 0;
+  // packed launch of uneven GL1D batches (built per vector-group size): slot map, CTA count, slots/thread
+  void* pack_map = nullptr;
+  int pack_kg = 0, pack_count = 0, pack_ppt = 0;
   // Crank-Nicolson (scheme = RSV_SCHEME_CN): host copies of the tridiagonal coefficients (FP64,
   // direct then adjoint: lo, di, up) and, per step h, the cyclic-reduction factors of
   // I - h/2 A on the device: [dir][level][n] for both neighbours, then [dir][n] inverse pivots
@@ -174,6 +197,12 @@ struct rsv_operator_s {
   };
   std::vector<ProbeMemo> probe_memo;
   int last_tile = 0, last_group = 0;   // tile length and vector-group size of the latest march
+  // CUDA graphs of tile launch sequences (ops.cu), the private capture stream, replays so far
+  std::vector<rsv::TileGraph> tile_graphs;
+  cudaStream_t cap_stream = nullptr;
+  int64_t graph_replays = 0;
+  // autotuned tile length and vector group (rsv_autotune) for marches of tuned_k vectors
+  int tuned_k = 0, tuned_tile = 0, tuned_group = 0;
   int64_t last_steps = 0;              // steps marched by the latest march's last vector group
 
   ~rsv_operator_s();
@@ -266,6 +295,11 @@ cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y,
 template <typename R>
 cudaError_t launch_gl1d_apply(const Gl1dTile& t, const int32_t* inst_of_point, const void* x, void* y,
                               cudaStream_t st);
+// Batches of uneven instances: CTAs of 1024 threads x ppt slots holding several (instance, vector)
+// segments each (map [n_packs][1024 ppt] of rows, -1 for separators and unused slots).
+template <typename R>
+cudaError_t launch_gl1d_pack(const Gl1dTile& t, const int32_t* map, int n_packs, int ppt, void* u, const void* F,
+                             void* Y, int* flag, cudaStream_t st);
 
 // ----- glue (glue_kernels.cu) ----------------------------------------------
 // G[j][i][a][b] = sum_{p in instance i} conj(X[j][a][p]) X[j][b][p]

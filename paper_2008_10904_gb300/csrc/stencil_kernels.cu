@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdlib>
 #include <utility>
@@ -565,12 +566,10 @@ __global__ void __launch_bounds__(kFThreads) adr2d_step_kernel(StGeom g, const R
 template <typename R>
 cudaError_t launch_adr2d_step(rsv_operator op, const StGeom& g, const R* uin, R* uout, const R* f0, const R* fh,
                               const R* f1, R* ysnap, R h) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(adr2d_step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)adr2d_fused_smem<R>());
-    attr = true;
-  }
+  // per-device attribute: set before every launch (cheap next to a step over the whole grid)
+  cudaError_t ae = cudaFuncSetAttribute(adr2d_step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)adr2d_fused_smem<R>());
+  if (ae != cudaSuccess) return ae;
   dim3 grid((unsigned)((g.nx + kFTX - 1) / kFTX), (unsigned)((g.ny + kFTY - 1) / kFTY), (unsigned)g.kg);
   adr2d_step_kernel<R><<<grid, kFThreads, adr2d_fused_smem<R>(), op->stream>>>(g, uin, uout, f0, fh, f1, ysnap, h);
   return cudaGetLastError();
@@ -912,22 +911,28 @@ int pair3d_zchunks(int per_chunk, int nz, int resident) {
 
 template <bool ADJ, bool PAIR_B, int MINB>
 cudaError_t launch_pair3d_minb(rsv_operator op, const StGeom& g, const Pair3D& P0) {
-  static int attr_dev[64] = {0};
+  // the shared-memory opt-in and the residency are per device; set up once per device under a lock
+  static std::mutex mu;
   static int resident_dev[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_dev[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(adv3d_pair_kernel<ADJ, PAIR_B, MINB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3Smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adv3d_pair_kernel<ADJ, PAIR_B, MINB>, k3Threads,
-                                                      k3Smem);
-    if (e != cudaSuccess) return e;
-    resident_dev[dev] = std::max(1, per_sm) * std::max(1, op->sm_count);
-    attr_dev[dev] = 1;
+  int resident = std::max(1, op->sm_count);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || resident_dev[dev] == 0) {
+      cudaError_t e = cudaFuncSetAttribute(adv3d_pair_kernel<ADJ, PAIR_B, MINB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3Smem);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adv3d_pair_kernel<ADJ, PAIR_B, MINB>, k3Threads,
+                                                        k3Smem);
+      if (e != cudaSuccess) return e;
+      resident = std::max(1, per_sm) * std::max(1, op->sm_count);
+      if (dev >= 0 && dev < 64) resident_dev[dev] = resident;
+    } else {
+      resident = resident_dev[dev];
+    }
   }
-  const int resident = (dev >= 0 && dev < 64) ? resident_dev[dev] : op->sm_count;
   const unsigned ntx = (unsigned)((g.nx + k3TX - 1) / k3TX), nty = (unsigned)((g.ny + k3TY - 1) / k3TY);
   Pair3D P = P0;
   P.zchunks = pair3d_zchunks((int)(ntx * nty) * g.kg, g.nz, resident);

@@ -103,6 +103,8 @@ _ENTRY_POINTS = {
                                           ctypes.POINTER(ctypes.c_double)]),
     "rsv_apply_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_void_p]),
+    "rsv_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(rsv_march_opts),
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "rsv_series_march": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                         ctypes.POINTER(rsv_series_opts), ctypes.c_void_p, ctypes.c_int64,
@@ -302,6 +304,14 @@ def rsv_orthonormalize(op: Operator, block, k: int, r_factor: np.ndarray | None 
 
 def rsv_apply_operator(op: Operator, x, k: int, adjoint: bool, y):
     _check(_lib.rsv_apply_operator(op.handle, _ptr(x), int(k), int(bool(adjoint)), _ptr(y)))
+
+
+def rsv_autotune(op: Operator, f_hat, k: int, **opts):
+    """Measured (tile length, vector group) for marches of k vectors; kept in the operator."""
+    o = _opts(**opts)
+    t, g = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.rsv_autotune(op.handle, _ptr(f_hat), int(k), ctypes.byref(o), ctypes.byref(t), ctypes.byref(g)))
+    return t.value, g.value
 
 
 def _f64(x):
