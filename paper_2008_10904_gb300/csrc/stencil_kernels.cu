@@ -42,6 +42,7 @@ struct StGeom {
   const void* f1;
   const void* f2;
   const void* f3;
+  const void* f4;         // ADV3D, FP32: the four fields interleaved per cell (float4: U, dU/dx, dU/dy, dU/dz)
   int sponge_cells;
   double sponge_amp;
   bool adjoint;
@@ -420,6 +421,7 @@ StGeom geom_of(rsv_operator op, int kg, bool adjoint) {
   g.f1 = op->fld[1];
   g.f2 = op->fld[2];
   g.f3 = op->fld[3];
+  g.f4 = op->fld[4];
   g.sponge_cells = op->sponge_cells;
   g.sponge_amp = op->sponge_amp;
   g.adjoint = adjoint;
@@ -656,16 +658,27 @@ __device__ __forceinline__ void op3d_smem(const float* __restrict__ xb, const fl
 }
 
 // Base-flow fields at cell offset q (x index i), for the forward or transposed operator.
+// Forward: one 16-byte load of the interleaved fields.  Transposed: U at the two x neighbours and
+// the gradient as separate loads (the interleaved load measured 12% slower there).
 template <bool ADJ>
 __device__ __forceinline__ Bf load_bf(const StGeom& g, int q, int i, bool ok) {
   const float* U = reinterpret_cast<const float*>(g.f0);
+  Bf b;
+  if (!ADJ) {
+    const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(g.f4) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    b.Uc = v.x;
+    b.Uw = b.Ue = 0.f;
+    b.Ux = v.y;
+    b.Uy = v.z;
+    b.Uz = v.w;
+    return b;
+  }
   const float* Ux = reinterpret_cast<const float*>(g.f1);
   const float* Uy = reinterpret_cast<const float*>(g.f2);
   const float* Uz = reinterpret_cast<const float*>(g.f3);
-  Bf b;
-  b.Uc = (!ADJ && ok) ? __ldg(U + q) : 0.f;
-  b.Uw = (ADJ && ok && i > 0) ? __ldg(U + q - 1) : 0.f;
-  b.Ue = (ADJ && ok && i < g.nx - 1) ? __ldg(U + q + 1) : 0.f;
+  b.Uc = 0.f;
+  b.Uw = (ok && i > 0) ? __ldg(U + q - 1) : 0.f;
+  b.Ue = (ok && i < g.nx - 1) ? __ldg(U + q + 1) : 0.f;
   b.Ux = ok ? __ldg(Ux + q) : 0.f;
   b.Uy = ok ? __ldg(Uy + q) : 0.f;
   b.Uz = ok ? __ldg(Uz + q) : 0.f;
@@ -679,21 +692,37 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
 }
 
 // Per-thread registers of one plane's point inputs, loaded one plane ahead of their use.
+template <int S1>
 struct Stage1In {
-  float f[k3S1][3];    // forcing of the first stage
-  float u[k3S1][3];    // pair B: the state u
-  Bf bf[k3S1];         // base flow
+  float f[S1][3];      // forcing of the first stage
+  float u[S1][3];      // pair B: the state u
+  Bf bf[S1];           // base flow
 };
+template <int S2>
 struct Stage2In {
-  float f[k3S2][3];    // forcing of the second stage
-  float u[k3S2][3];    // pair B: the state u
-  float a[k3S2][3];    // pair B: the accumulator
-  Bf bf[k3S2];         // base flow
+  float f[S2][3];      // forcing of the second stage
+  float u[S2][3];      // pair B: the state u
+  float a[S2][3];      // pair B: the accumulator
+  Bf bf[S2];           // base flow
 };
 
+// Tile height TY and threads NT of a pair-kernel variant: 64 x 8 with 256 threads (two CTAs per SM)
+// or 64 x 16 with 512 threads (one CTA per SM, less halo work per output cell).
+template <int TY>
+constexpr size_t pair3d_smem() {
+  return sizeof(float) * (4 * 3 * (size_t)((k3TX + 8) * (TY + 4)) + 3 * 3 * (size_t)((k3TX + 2) * (TY + 2)));
+}
+
 // Requires nx % 4 == 0 (16-byte rows of the input ring) and n < 2^31 (32-bit offsets in a vector).
-template <bool ADJ, bool PAIR_B, int MINB>
-__global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, Pair3D P) {
+template <bool ADJ, bool PAIR_B, int MINB, int TY, int NT>
+__global__ void __launch_bounds__(NT, MINB) adv3d_pair_kernel(StGeom g, Pair3D P) {
+  // this variant's tile geometry (the namespace-level constants describe the 64 x 8 variant)
+  constexpr int k3TY = TY, k3Threads = NT;
+  constexpr int k3UH = k3TY + 4, k3XH = k3TY + 2;
+  constexpr int k3UP = k3UW * k3UH, k3XP = k3XW * k3XH;
+  constexpr int k3S1 = (k3XP + k3Threads - 1) / k3Threads;
+  constexpr int k3S2 = k3TX * k3TY / k3Threads;
+  static_assert(k3TX * k3TY % k3Threads == 0, "whole second-stage cells per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);            // [4 planes][3 comps][k3UP]
   float* mid = ring + 4 * 3 * k3UP;                              // [3 planes][3 comps][k3XP]
@@ -767,7 +796,7 @@ __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, P
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  auto fetch1 = [&](int kz, Stage1In& r) {
+  auto fetch1 = [&](int kz, Stage1In<k3S1>& r) {
     const bool zin = kz >= 0 && kz < nz;
 #pragma unroll
     for (int sl = 0; sl < k3S1; ++sl) {
@@ -781,7 +810,7 @@ __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, P
       r.bf[sl] = load_bf<ADJ>(g, q, gi1[sl], ok);
     }
   };
-  auto fetch2 = [&](int kz, Stage2In& r) {
+  auto fetch2 = [&](int kz, Stage2In<k3S2>& r) {
     const bool zin = kz >= z0 && kz < z1;
 #pragma unroll
     for (int sl = 0; sl < k3S2; ++sl) {
@@ -798,7 +827,7 @@ __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, P
   };
 
   // first stage on plane kz, tile + 1 halo cell: x_mid = u + c1 (A x + f_a); zero outside the grid
-  auto first_stage = [&](int kz, const Stage1In& r) {
+  auto first_stage = [&](int kz, const Stage1In<k3S1>& r) {
     float* dst = mid + (size_t)(((kz % 3) + 3) % 3) * 3 * k3XP;
     const float* xb = ring + (size_t)((kz - 1) & 3) * 3 * k3UP;
     const float* xc = ring + (size_t)(kz & 3) * 3 * k3UP;
@@ -824,7 +853,7 @@ __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, P
   };
 
   // second stage on plane kz, the tile
-  auto second_stage = [&](int kz, const Stage2In& r) {
+  auto second_stage = [&](int kz, const Stage2In<k3S2>& r) {
     const float* mb = mid + (size_t)((((kz - 1) % 3) + 3) % 3) * 3 * k3XP;
     const float* mc = mid + (size_t)(kz % 3) * 3 * k3XP;
     const float* mt = mid + (size_t)((kz + 1) % 3) * 3 * k3XP;
@@ -857,8 +886,8 @@ __global__ void __launch_bounds__(k3Threads, MINB) adv3d_pair_kernel(StGeom g, P
     }
   };
 
-  Stage1In s1;
-  Stage2In s2;
+  Stage1In<k3S1> s1;
+  Stage2In<k3S2> s2;
   // prologue: planes z0 - 2 .. z0 + 1 of the stencil input; first stage on plane z0 - 1
   for (int kz = z0 - 2; kz <= z0 + 1; ++kz) load_plane(kz);
   fetch1(z0 - 1, s1);
@@ -909,8 +938,9 @@ int pair3d_zchunks(int per_chunk, int nz, int resident) {
   return best;
 }
 
-template <bool ADJ, bool PAIR_B, int MINB>
+template <bool ADJ, bool PAIR_B, int MINB, int TY, int NT>
 cudaError_t launch_pair3d_minb(rsv_operator op, const StGeom& g, const Pair3D& P0) {
+  constexpr size_t smem = pair3d_smem<TY>();
   // the shared-memory opt-in and the residency are per device; set up once per device under a lock
   static std::mutex mu;
   static int resident_dev[64] = {0};
@@ -920,12 +950,12 @@ cudaError_t launch_pair3d_minb(rsv_operator op, const StGeom& g, const Pair3D& P
   {
     std::lock_guard<std::mutex> lock(mu);
     if (dev < 0 || dev >= 64 || resident_dev[dev] == 0) {
-      cudaError_t e = cudaFuncSetAttribute(adv3d_pair_kernel<ADJ, PAIR_B, MINB>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3Smem);
+      cudaError_t e = cudaFuncSetAttribute(adv3d_pair_kernel<ADJ, PAIR_B, MINB, TY, NT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adv3d_pair_kernel<ADJ, PAIR_B, MINB>, k3Threads,
-                                                        k3Smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adv3d_pair_kernel<ADJ, PAIR_B, MINB, TY, NT>, NT,
+                                                        smem);
       if (e != cudaSuccess) return e;
       resident = std::max(1, per_sm) * std::max(1, op->sm_count);
       if (dev >= 0 && dev < 64) resident_dev[dev] = resident;
@@ -933,17 +963,28 @@ cudaError_t launch_pair3d_minb(rsv_operator op, const StGeom& g, const Pair3D& P
       resident = resident_dev[dev];
     }
   }
-  const unsigned ntx = (unsigned)((g.nx + k3TX - 1) / k3TX), nty = (unsigned)((g.ny + k3TY - 1) / k3TY);
+  const unsigned ntx = (unsigned)((g.nx + k3TX - 1) / k3TX), nty = (unsigned)((g.ny + TY - 1) / TY);
   Pair3D P = P0;
   P.zchunks = pair3d_zchunks((int)(ntx * nty) * g.kg, g.nz, resident);
   const unsigned blocks = ntx * nty * (unsigned)P.zchunks * (unsigned)g.kg;
-  adv3d_pair_kernel<ADJ, PAIR_B, MINB><<<blocks, k3Threads, k3Smem, op->stream>>>(g, P);
+  adv3d_pair_kernel<ADJ, PAIR_B, MINB, TY, NT><<<blocks, NT, smem, op->stream>>>(g, P);
   return cudaGetLastError();
+}
+
+// Tile height of the pair kernels: 8 (default) or 16 (RSV_PAIR3D_TY=16), read once per process.
+int pair3d_ty() {
+  static int v = [] {
+    const char* e = getenv("RSV_PAIR3D_TY");
+    return (e != nullptr && atoi(e) == 16) ? 16 : 8;
+  }();
+  return v;
 }
 
 template <bool ADJ, bool PAIR_B>
 cudaError_t launch_pair3d(rsv_operator op, const StGeom& g, const Pair3D& P) {
-  return pair3d_minb() == 2 ? launch_pair3d_minb<ADJ, PAIR_B, 2>(op, g, P) : launch_pair3d_minb<ADJ, PAIR_B, 3>(op, g, P);
+  if (pair3d_ty() == 16) return launch_pair3d_minb<ADJ, PAIR_B, 1, 16, 512>(op, g, P);
+  return pair3d_minb() == 2 ? launch_pair3d_minb<ADJ, PAIR_B, 2, 8, 256>(op, g, P)
+                            : launch_pair3d_minb<ADJ, PAIR_B, 3, 8, 256>(op, g, P);
 }
 
 // RSV_STENCIL3D_STAGED=1 keeps FP32 3-D marches on the four single-stage kernels (comparisons).
@@ -1062,7 +1103,17 @@ rsv_status build_adv3d(rsv_operator op, const rsv_operator_desc* d) {
         Uy[q] = r > 0 ? gg * (y / (r * del)) : 0.0;
         Uz[q] = r > 0 ? gg * (z / (r * del)) : 0.0;
       }
-  return upload_fields(op, {U, Ux, Uy, Uz});
+  rsv_status st = upload_fields(op, {U, Ux, Uy, Uz});
+  if (st != RSV_OK || op->prec != RSV_PREC_FP32) return st;
+  // the pair kernels read the four fields of a cell with one 16-byte load
+  std::vector<float> il(4 * U.size());
+  for (size_t q = 0; q < U.size(); ++q) {
+    il[4 * q] = (float)U[q];
+    il[4 * q + 1] = (float)Ux[q];
+    il[4 * q + 2] = (float)Uy[q];
+    il[4 * q + 3] = (float)Uz[q];
+  }
+  return upload(op, il.data(), il.size() * sizeof(float), &op->fld[4]);
 }
 
 // Workspace behind the state in the march: two stage-input buffers and the accumulator.

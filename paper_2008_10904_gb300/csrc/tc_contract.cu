@@ -277,13 +277,15 @@ __global__ void __launch_bounds__(256, 1) tc_contract_kernel(ContractArgs a) {
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int round16c(int x) { return (x + 15) / 16 * 16; }
 
-constexpr int kRawRing = 4;
+// Ring depths: the twiddle operand of every sub-tile streams from L2 (about 512 KB per row tile), so
+// its ring is four chunks deep; a slot holds one sub-tile's 256 rows (hi and lo), half of a global
+// chunk.  The raw long-operand ring is eight chunks deep.  Total 224.25 KB of shared memory.
+constexpr int kRawRing = 8;
 constexpr int kAStages = 2;
-constexpr int kBRing = 2;
+constexpr int kBRing = 4;
+constexpr uint32_t kBRingFloats = 256 * kKc;          // per hi / lo: one sub-tile's rows
 constexpr uint32_t kRawBytes = kRowsCta * kKc * 4;   // 128 rows x 16 real K values
 constexpr int kPipeThreads = 480;                    // 15 warps, roles below
-constexpr uint32_t kPipeSmem =
-    kRawRing * kRawBytes + kAStages * 2 * kAStageFloats * 4 + kBRing * 2 * kBStageFloats * 4 + 256;
 
 struct PipeBars {
   uint64_t raw_full[kRawRing], raw_empty[kRawRing];
@@ -292,6 +294,13 @@ struct PipeBars {
   uint64_t acc_full[2], acc_empty[2];   // two tensor-memory accumulators of 256 columns
   int abort_flag;
 };
+
+// the barriers sit behind the operand rings; their reserve is sizeof(PipeBars) rounded up
+constexpr uint32_t kPipeBarBytes = (uint32_t)((sizeof(PipeBars) + 127) / 128 * 128);
+constexpr uint32_t kPipeSmem =
+    kRawRing * kRawBytes + kAStages * 2 * kAStageFloats * 4 + kBRing * 2 * kBRingFloats * 4 + kPipeBarBytes;
+// dynamic shared memory plus up to 1 KB for the static variable and the 1024-byte alignment
+static_assert(kPipeSmem + 1024 <= 232448, "pipelined contraction exceeds the shared memory of a CTA");
 
 __device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   return tc::mbar_wait(bar, parity, 0xFFFFFFFFu, abort_flag);
@@ -425,7 +434,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
   unsigned char* raw = smem;                                                     // [kRawRing][kRawBytes]
   float* sA = reinterpret_cast<float*>(smem + kRawRing * kRawBytes);             // [kAStages][hi, lo][..]
   float* sB = sA + kAStages * 2 * kAStageFloats;                                 // [kBRing][hi, lo][..]
-  PipeBars* pb = reinterpret_cast<PipeBars*>(sB + kBRing * 2 * kBStageFloats);
+  PipeBars* pb = reinterpret_cast<PipeBars*>(sB + kBRing * 2 * kBRingFloats);
   __shared__ uint32_t tbase;
   volatile int* abort_flag = &pb->abort_flag;
 
@@ -496,11 +505,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
           for (int kc = 0; kc < chunks; ++kc, ++g) {
             const uint32_t bs = g % kBRing, bu = g / kBRing;
             if (bu > 0 && !pwait(&pb->b_empty[bs], (bu - 1) & 1, abort_flag)) { ok = false; break; }
-            float* B_hi = sB + bs * 2 * kBStageFloats;
+            float* B_hi = sB + bs * 2 * kBRingFloats;
             const float* bsrc = a.B + (size_t)kc * 2 * kBStageFloats + (size_t)h * 256 * kKc;
             tc::mbar_arrive_expect_tx(&pb->b_full[bs], 2 * bytes);
             tc::bulk_g2s(B_hi, bsrc, bytes, &pb->b_full[bs]);
-            tc::bulk_g2s(B_hi + kBStageFloats, bsrc + kBStageFloats, bytes, &pb->b_full[bs]);
+            tc::bulk_g2s(B_hi + kBRingFloats, bsrc + kBStageFloats, bytes, &pb->b_full[bs]);
           }
         }
       }
@@ -535,8 +544,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) tc_contract_pipe_kernel(Contr
             tc::tc_fence_after();
             const char* A_hi = reinterpret_cast<const char*>(sA + as * 2 * kAStageFloats);
             const char* A_lo = A_hi + 4 * kAStageFloats;
-            const char* B_hi = reinterpret_cast<const char*>(sB + bs * 2 * kBStageFloats);
-            const char* B_lo = B_hi + 4 * kBStageFloats;
+            const char* B_hi = reinterpret_cast<const char*>(sB + bs * 2 * kBRingFloats);
+            const char* B_lo = B_hi + 4 * kBRingFloats;
 #pragma unroll
             for (int ks = 0; ks < kKc / 8; ++ks) {
               const uint64_t ah = tc::smem_desc(A_hi + ks * 256, 128, sbo);
