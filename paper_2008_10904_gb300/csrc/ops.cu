@@ -184,11 +184,13 @@ int march_tile_kernels(rsv_operator op, int steps, int kg) {
       return steps + 1;
     case RSV_OP_ADR2D: {
       const char* e = getenv("RSV_STENCIL_FUSED");
-      return (e != nullptr && e[0] == '1') ? steps + 1 : 4 * steps + 1;   // per-stage kernels by default
+      if (e != nullptr && e[0] == '1') return steps + 1;
+      const bool pairs = op->prec == RSV_PREC_FP32 && adr2d_pairs_enabled() && op->nx % 4 == 0 &&
+                         op->n < ((int64_t)1 << 31);
+      return pairs ? 2 * steps + 1 : 4 * steps + 1;   // two stage-pair kernels per step, or four stages
     }
     case RSV_OP_ADV3D: {
-      const char* e = getenv("RSV_STENCIL3D_STAGED");
-      const bool pairs = op->prec == RSV_PREC_FP32 && !op->bf16_state && !(e != nullptr && e[0] == '1') &&
+      const bool pairs = op->prec == RSV_PREC_FP32 && !op->bf16_state && adv3d_pairs_enabled() &&
                          op->nx % 4 == 0 && op->n < ((int64_t)1 << 31);
       return pairs ? 2 * steps + 1 : 4 * steps + 1;   // two stage-pair kernels per step, or four stages
     }

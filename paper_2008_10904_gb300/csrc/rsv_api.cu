@@ -256,7 +256,10 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
   }
   if (op->kind == RSV_OP_ADR2D) {
     const char* e = getenv("RSV_STENCIL_FUSED");
-    if (e != nullptr && e[0] == '1') path = "cuda-core whole-step kernel";
+    if (e != nullptr && e[0] == '1')
+      path = "cuda-core whole-step kernel";
+    else if (op->prec == RSV_PREC_FP32 && adr2d_pairs_enabled() && op->nx % 4 == 0 && op->n < ((int64_t)1 << 31))
+      path = "cuda-core 2-D stage-pair kernels";
   }
   if (op->kind == RSV_OP_DENSE) {
     if (op->prec == RSV_PREC_FP32 && op->tc_tiles[0] && !op->tc_disabled)

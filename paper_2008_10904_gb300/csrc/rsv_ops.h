@@ -69,6 +69,9 @@ cudaError_t dense_tc_march_tile(rsv_operator op, int kg, bool adjoint, int64_t n
 
 // structured-grid kinds (stencil_kernels.cu)
 size_t stencil_scratch_bytes(rsv_operator op, int kg);
+// whether FP32 marches of the 2-D / 3-D kind use the stage-pair kernels (environment switches)
+bool adr2d_pairs_enabled();
+bool adv3d_pairs_enabled();
 template <typename R>
 cudaError_t stencil_march_tile(rsv_operator op, const MarchTile& t, void* state, const void* F, void* Y);
 template <typename R>

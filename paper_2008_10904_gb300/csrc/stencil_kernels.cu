@@ -912,6 +912,153 @@ __global__ void __launch_bounds__(NT, MINB) adv3d_pair_kernel(StGeom g, Pair3D P
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// ---------------------------------------------------------------------------
+// 2-D system, FP32: RK4 in two launches per step, each fusing a pair of stages (the scheme of the
+// 3-D pair kernels above, on one plane).  A CTA owns a 64 x 32 tile of one vector: the pair's
+// stencil input (u or x3) is copied with a halo of two cells into shared memory (16-byte
+// asynchronous copies of rows from x = X0 - 4), the first stage is evaluated on the tile and a
+// one-cell halo into a second shared array, the second stage on the tile.  Per step the
+// state-sized arrays cross HBM about 11 times (pair A: u and two forcing samples read, x3 and acc
+// written, plus the snapshot on analysed steps; pair B: x3, u, acc and two forcing samples read,
+// u' written) against about 20 for the four single-stage kernels.  Cells outside the grid hold zero.
+// ---------------------------------------------------------------------------
+constexpr int k2TX = 64, k2TY = 32, k2Threads = 256;
+constexpr int k2UW = k2TX + 8, k2UH = k2TY + 4;     // input tile: x from X0 - 4, y halo 2
+constexpr int k2XW = k2TX + 2, k2XH = k2TY + 2;     // first-stage tile: halo 1
+constexpr int k2Row4 = k2UW / 4;
+
+// Sponge rate at cell (gi, gj) with precomputed 1 / sponge_cells (the same values as sponge()).
+__device__ __forceinline__ float sponge_fast(int gi, int gj, const StGeom& g, float inv_s) {
+  const int d = min(min(gi, g.nx - 1 - gi), min(gj, g.ny - 1 - gj));
+  if (d >= g.sponge_cells) return 0.f;
+  const float t = (float)(g.sponge_cells - d) * inv_s;
+  return (float)g.sponge_amp * t * t;
+}
+
+// Requires nx % 4 == 0 (16-byte rows of the input tile and of the second stage's float4 accesses).
+template <bool PAIR_B>
+__global__ void __launch_bounds__(k2Threads) adr2d_pair_kernel(StGeom g, Pair3D P) {
+  __shared__ __align__(16) float tin[k2UH * k2UW];
+  __shared__ float mid[k2XH * k2XW];
+  __shared__ float rowc[k2XH][3];            // per row of the first-stage tile: cw, ce, diagonal without sponge
+  const int nx = g.nx, ny = g.ny;
+  int b = blockIdx.x;
+  const int v = b % g.kg;       // vector fastest: the tiles of all vectors of a region run together
+  b /= g.kg;
+  const int ntx = (nx + k2TX - 1) / k2TX;
+  const int X0 = (b % ntx) * k2TX, Y0 = (b / ntx) * k2TY;
+  const int64_t base = (int64_t)v * g.n;
+  const float* __restrict__ in = P.in + base;
+  const float* __restrict__ fa = P.fa ? P.fa + base : nullptr;
+  const float* __restrict__ fb = P.fb ? P.fb + base : nullptr;
+  const float* __restrict__ pu = PAIR_B ? P.u + base : nullptr;
+  const float* __restrict__ pacc = PAIR_B ? P.acc + base : nullptr;
+  float* __restrict__ out = P.out + base;
+  float* __restrict__ acc_out = PAIR_B ? nullptr : P.acc_out + base;
+  float* __restrict__ ysnap = P.ysnap ? P.ysnap + base : nullptr;
+  const float i2dx = 0.5f / (float)g.dx, idx2 = 1.f / ((float)g.dx * (float)g.dx);
+  const float idy2 = 1.f / ((float)g.dy * (float)g.dy), nu = (float)g.visc;
+  const float cy = nu * idy2;
+  const float inv_s = g.sponge_cells > 0 ? 1.f / (float)g.sponge_cells : 0.f;
+  // the sponge touches this tile (with its halo) only near a wall
+  const bool near_wall = X0 - 1 < g.sponge_cells || X0 + k2TX + 1 > nx - g.sponge_cells || Y0 - 1 < g.sponge_cells ||
+                         Y0 + k2TY + 1 > ny - g.sponge_cells;
+  const float h = P.h;
+  const float c1 = PAIR_B ? h : 0.5f * h;
+  const float c2 = PAIR_B ? h / 6.f : 0.5f * h;
+  const int tid = threadIdx.x;
+  // the pair's stencil input with a two-cell halo; 16-byte chunks lie wholly inside or outside
+  for (int e = tid; e < k2UH * k2Row4; e += k2Threads) {
+    const int ly = e / k2Row4, ch = e - ly * k2Row4;
+    const int gj = Y0 - 2 + ly, gx = X0 - 4 + 4 * ch;
+    float* d = tin + ly * k2UW + 4 * ch;
+    if (gj >= 0 && gj < ny && gx >= 0 && gx < nx)
+      cp_async16(d, in + (int64_t)gj * nx + gx);
+    else
+      *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  if (tid < k2XH) {   // row coefficients of rows Y0 - 1 .. Y0 + k2TY
+    const int gj = min(max(Y0 - 1 + tid, 0), ny - 1);
+    const float* U = reinterpret_cast<const float*>(g.f0);
+    const float* rr = reinterpret_cast<const float*>(g.f1);
+    const float ux = g.adjoint ? -__ldg(U + gj) : __ldg(U + gj);
+    rowc[tid][0] = ux * i2dx + nu * idx2;
+    rowc[tid][1] = -ux * i2dx + nu * idx2;
+    rowc[tid][2] = -2.f * nu * (idx2 + idy2) + __ldg(rr + gj);
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  // first stage on the tile and a one-cell halo: x_mid = u + c1 (A x + f_a); zero outside the grid
+  for (int e = tid; e < k2XH * k2XW; e += k2Threads) {
+    const int lx = e % k2XW, ly = e / k2XW;
+    const int gi = X0 - 1 + lx, gj = Y0 - 1 + ly;
+    float xo = 0.f;
+    if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+      const int et = (ly + 1) * k2UW + lx + 3;      // tin index of (gi, gj)
+      const int64_t q = (int64_t)gj * nx + gi;
+      const float cc = rowc[ly][2] - (near_wall ? sponge_fast(gi, gj, g, inv_s) : 0.f);
+      const float k = rowc[ly][0] * tin[et - 1] + rowc[ly][1] * tin[et + 1] + cy * (tin[et - k2UW] + tin[et + k2UW]) +
+                      cc * tin[et] + (fa ? fa[q] : 0.f);
+      const float uu = PAIR_B ? pu[q] : tin[et];
+      xo = uu + c1 * k;
+    }
+    mid[e] = xo;
+  }
+  __syncthreads();
+  // second stage on the tile, four cells along x per item (16-byte global accesses)
+  for (int e = tid; e < k2TX * k2TY / 4; e += k2Threads) {
+    const int tx = 4 * (e % (k2TX / 4)), ty = e / (k2TX / 4);
+    const int gi0 = X0 + tx, gj = Y0 + ty;
+    if (gi0 >= nx || gj >= ny) continue;
+    const int64_t q = (int64_t)gj * nx + gi0;
+    const int ly = ty + 1;                          // row of the first-stage tile
+    const float cw = rowc[ly][0], ce = rowc[ly][1], cd = rowc[ly][2];
+    const float4 f4 = fb ? ld4(fb + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 kk, xm;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int em = ly * k2XW + tx + c + 1;
+      const float cc = cd - (near_wall ? sponge_fast(gi0 + c, gj, g, inv_s) : 0.f);
+      const float k = cw * mid[em - 1] + ce * mid[em + 1] + cy * (mid[em - k2XW] + mid[em + k2XW]) + cc * mid[em] +
+                      get4(f4, c);
+      set4(kk, c, k);
+      set4(xm, c, mid[em]);
+    }
+    if (!PAIR_B) {
+      const float* urow = tin + (ty + 2) * k2UW + tx + 4;
+      const float4 uu = make_float4(urow[0], urow[1], urow[2], urow[3]);
+      float4 o3, oa;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float u1 = get4(uu, c), k = get4(kk, c);
+        set4(o3, c, u1 + c2 * k);                                             // x3
+        set4(oa, c, u1 + (get4(xm, c) - u1) * (1.f / 3.f) + (h / 3.f) * k);  // u + h/6 k1 + h/3 k2
+      }
+      st4(out + q, o3);
+      st4(acc_out + q, oa);
+      if (ysnap) st4(ysnap + q, uu);
+    } else {
+      const float4 uu = ld4(pu + q), a4 = ld4(pacc + q);
+      float4 o;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float u1 = get4(uu, c);
+        const float a = get4(a4, c) + (get4(xm, c) - u1) * (1.f / 3.f);    // + h/3 k3
+        set4(o, c, a + c2 * get4(kk, c));                                    // + h/6 k4
+      }
+      st4(out + q, o);
+    }
+  }
+}
+
+template <bool PAIR_B>
+cudaError_t launch_pair2d(rsv_operator op, const StGeom& g, const Pair3D& P) {
+  const unsigned ntx = (unsigned)((g.nx + k2TX - 1) / k2TX), nty = (unsigned)((g.ny + k2TY - 1) / k2TY);
+  adr2d_pair_kernel<PAIR_B><<<ntx * nty * (unsigned)g.kg, k2Threads, 0, op->stream>>>(g, P);
+  return cudaGetLastError();
+}
+
 // Resident CTAs per SM the pair kernels are compiled for: 2 (no spills, the default) or 3 (80
 // registers, spills); RSV_PAIR3D_MINB selects (read once per process).
 int pair3d_minb() {
@@ -987,12 +1134,6 @@ cudaError_t launch_pair3d(rsv_operator op, const StGeom& g, const Pair3D& P) {
                             : launch_pair3d_minb<ADJ, PAIR_B, 3, 8, 256>(op, g, P);
 }
 
-// RSV_STENCIL3D_STAGED=1 keeps FP32 3-D marches on the four single-stage kernels (comparisons).
-bool adv3d_pairs_enabled() {
-  const char* e = getenv("RSV_STENCIL3D_STAGED");
-  return !(e != nullptr && e[0] == '1');
-}
-
 // RSV_STENCIL_FUSED=1 selects the whole-step kernel (read at each march tile).  The
 // per-stage float4 kernels stay the default: on GB300 they measured 5% faster at the
 // 1024 x 512 x 16 workload although they move more bytes.
@@ -1039,6 +1180,21 @@ cudaError_t launch_stage(rsv_operator op, const StGeom& g, const R* xin, const R
 }
 
 }  // namespace
+
+// RSV_STENCIL3D_STAGED=1 keeps FP32 3-D marches on the four single-stage kernels (comparisons).
+bool adv3d_pairs_enabled() {
+  const char* e = getenv("RSV_STENCIL3D_STAGED");
+  return !(e != nullptr && e[0] == '1');
+}
+
+// RSV_STENCIL2D_STAGED=1 keeps FP32 2-D marches on the four single-stage kernels (comparisons).
+bool adr2d_pairs_enabled() {
+  static const bool v = [] {
+    const char* e = getenv("RSV_STENCIL2D_STAGED");
+    return !(e != nullptr && e[0] == '1');
+  }();
+  return v;
+}
 
 // 2-D jet: U(y) = 0.5 (1 + tanh((0.5 - |y|)/delta)), r(y) = -kappa dU/dy, sponge on the fly.
 rsv_status build_adr2d(rsv_operator op, const rsv_operator_desc* d) {
@@ -1150,8 +1306,11 @@ cudaError_t stencil_march_tile(rsv_operator op, const MarchTile& t, void* state,
     if (e == cudaSuccess) e = check_finite(op, u, rows, true);
     return e;
   }
-  if (sizeof(R) == 4 && op->kind == RSV_OP_ADV3D && adv3d_pairs_enabled() && !op->bf16_state &&
-      op->nx % 4 == 0 && op->n < ((int64_t)1 << 31)) {
+  const bool pairs3d = sizeof(R) == 4 && op->kind == RSV_OP_ADV3D && adv3d_pairs_enabled() && !op->bf16_state &&
+                       op->nx % 4 == 0 && op->n < ((int64_t)1 << 31);
+  const bool pairs2d = sizeof(R) == 4 && op->kind == RSV_OP_ADR2D && adr2d_pairs_enabled() && op->nx % 4 == 0 &&
+                       op->n < ((int64_t)1 << 31);
+  if (pairs3d || pairs2d) {
     // two fused stage pairs per step; the state ping-pongs between u and xb, x3 lives in xa
     float* cur = reinterpret_cast<float*>(u);
     float* nxt = reinterpret_cast<float*>(xb);
@@ -1178,7 +1337,10 @@ cudaError_t stencil_march_tile(rsv_operator op, const MarchTile& t, void* state,
       pb.out = nxt;
       pb.acc_out = nullptr;
       pb.ysnap = nullptr;
-      if (t.adjoint) {
+      if (pairs2d) {   // the 2-D kernels take the direction from g.adjoint
+        e = launch_pair2d<false>(op, g, pa);
+        if (e == cudaSuccess) e = launch_pair2d<true>(op, g, pb);
+      } else if (t.adjoint) {
         e = launch_pair3d<true, false>(op, g, pa);
         if (e == cudaSuccess) e = launch_pair3d<true, true>(op, g, pb);
       } else {

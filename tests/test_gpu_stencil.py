@@ -225,3 +225,30 @@ def test_adv3d_step_paths(rsv, make, adjoint, path, monkeypatch):
         assert rel_rows(y.cpu().numpy().astype(np.complex128), ref) < TOL32
     finally:
         rsv.rsv_destroy_operator(op)
+
+
+def _adr_pair_tiles(variant="ssrm", k=2):
+    """nx a multiple of 4 over several 64 x 32 pair-kernel tiles, ragged at the far edges."""
+    sysm = W.ADR2D(nx=200, ny=70, lx=40.0, ly=10.0, sponge_cells=6)
+    om = np.linspace(0.0, 4.0, 8)
+    dx = sysm.lx / (sysm.nx + 1)
+    return W.Workload("adr_pair_tiles", sysm, om, 0.5 * dx, k, variant, n_transient_windows=1, tail_steps=60,
+                      n_power_iter=1, real_state=True, seed=W.SEED_BASE + 36)
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("variant", ["ssrm", "trm"])
+def test_adr2d_stage_pairs_multi_tile(rsv, adjoint, variant):
+    """FP32 2-D march through the stage-pair kernels on a grid of 4 x 3 ragged tiles."""
+    w = _adr_pair_tiles(variant)
+    op = rsv.create_for_workload(w, 1)
+    try:
+        assert "2-D stage-pair" in rsv.rsv_describe(op)
+        fh = W.test_block(w).astype(np.complex64).astype(np.complex128)
+        x = _dev(fh, 1)
+        y = x * 0
+        (rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct)(op, x, w.k, y, **rsv.march_opts_for(w, tile_steps=37))
+        ref = _oracle(w, _matrix(w), fh, adjoint)
+        assert rel_rows(y.cpu().numpy().astype(np.complex128), ref) < TOL32
+    finally:
+        rsv.rsv_destroy_operator(op)
