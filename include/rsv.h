@@ -134,7 +134,9 @@ typedef struct {
   int64_t tail_steps;           /* TRM: unforced steps after the forcing window
                                    (the cap on the tail when tail_tol > 0)          */
   int32_t tile_steps;           /* steps per time tile S (0 = library default)      */
-  int32_t reserved;             /* must be 0                                        */
+  int32_t group_vectors;        /* most test vectors marched together (0 = the
+                                   library's choice: all k, halved until the march
+                                   workspace fits, or rsv_autotune's choice)        */
   double tail_tol;              /* TRM: 0 = march the whole tail; > 0 = truncate the
                                    record by the state norm (Sec. 2.2; Sec. 3 marches
                                    until the norm is below 1e-9, Sec. 4 until it is
@@ -316,6 +318,20 @@ rsv_status rsv_orthonormalize(rsv_operator op, void* block, int32_t k, double* r
  * of the operator's element type (complex for every kind; real-state kinds
  * act on real and imaginary parts alike).  For testing the operator kernels. */
 rsv_status rsv_apply_operator(rsv_operator op, const void* x, int32_t k, int32_t adjoint, void* y);
+
+/* rsv_march_direct / rsv_march_adjoint with the input block in HOST memory
+ * (f_hat_host / y_hat_host: [n_omega][k][n] of the operator's element type;
+ * pinned memory lets the copies run asynchronously).  The march processes the
+ * vectors in groups (see rsv_march_opts.group_vectors); each group's slice of
+ * the block is copied to a device staging buffer on a second stream while the
+ * previous group marches (two staging buffers), so the host-to-device transfer
+ * overlaps the march.  Output as for the device versions (device y_hat /
+ * w_hat).  Returns when the march is done.  Errors: those of the device
+ * versions, OOM (staging buffers). */
+rsv_status rsv_march_direct_host(rsv_operator op, const void* f_hat_host, int32_t k, const rsv_march_opts* opts,
+                                 void* y_hat);
+rsv_status rsv_march_adjoint_host(rsv_operator op, const void* y_hat_host, int32_t k, const rsv_march_opts* opts,
+                                  void* w_hat);
 
 /* Measured choice of the march's time-tile length and vector-group size for
  * marches of k vectors with these options.  Candidates: the default tile and

@@ -130,6 +130,12 @@ rsv_operator_s::~rsv_operator_s() {
   for (rsv::TileGraph& g : tile_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (cap_stream) cudaStreamDestroy(cap_stream);
+  for (int i = 0; i < 2; ++i) {
+    if (ws_stage[i].ptr) cudaFree(ws_stage[i].ptr);
+    if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);
+    if (ev_free[i]) cudaEventDestroy(ev_free[i]);
+  }
+  if (copy_stream) cudaStreamDestroy(copy_stream);
   if (ws_scaled.ptr) cudaFree(ws_scaled.ptr);
   for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
 }
@@ -556,7 +562,7 @@ struct TileTrial {
 
 template <typename R>
 static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out,
-                             bool adjoint, int scaling, const TileTrial* trial = nullptr) {
+                             bool adjoint, int scaling, const TileTrial* trial = nullptr, bool host_in = false) {
   const double *s_in = nullptr, *s_out = nullptr;
   march_scalings(op, scaling, adjoint, &s_in, &s_out);
   Schedule sc;
@@ -570,6 +576,7 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
   int S = (opts && opts->tile_steps > 0) ? opts->tile_steps
                                          : (op->tuned_k == k ? op->tuned_tile : default_tile_steps(op));
   int kg = (op->tuned_k == k && !(opts && opts->tile_steps > 0)) ? op->tuned_group : k;
+  if (opts && opts->group_vectors > 0) kg = std::min(kg, (int)opts->group_vectors);
   if (trial) {
     S = trial->S;
     kg = trial->kg;
@@ -589,6 +596,7 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
       if (op->prec != RSV_PREC_FP64) b += (double)op->n_omega * rows_ * sizeof(cpx<double>);
       if (s_in) b += (double)op->n_omega * rows_ * coef_bytes(op);
       if (op->kind == RSV_OP_DENSE) b += 2.0 * op->n_omega * rows_ * 2 * sizeof(R);
+      if (host_in) b += 2.0 * op->n_omega * rows_ * coef_bytes(op);   // staging buffers
       return b;
     };
     // per-tile traffic (coefficients, FP64 accumulators) is amortised over S, while the vector
@@ -629,6 +637,35 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
       if (b) cudaEventDestroy(b);
     }
   } ev_guard{ev0, ev1};
+  // host input: each group's [n_omega][kv][n] slice is copied into a staging buffer on the copy stream
+  // while the previous group marches; a buffer is refilled once the group that used it two groups
+  // earlier has finished with it
+  if (host_in) {
+    const size_t sb = (size_t)op->n_omega * kg * n * ce;
+    for (int i = 0; i < 2; ++i) {
+      if ((st = ensure(op->ws_stage[i], sb)) != RSV_OK) return st;
+      if (!op->ev_copied[i] && (e = cudaEventCreateWithFlags(&op->ev_copied[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "staging events");
+      if (!op->ev_free[i] && (e = cudaEventCreateWithFlags(&op->ev_free[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "staging events");
+    }
+    if (!op->copy_stream && (e = cudaStreamCreateWithFlags(&op->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "copy stream");
+  }
+  auto stage_copy = [&](int gi) -> cudaError_t {   // group gi into staging buffer gi % 2
+    const int a0 = gi * kg;
+    const int kv = std::min(kg, k - a0);
+    const int b = gi & 1;
+    cudaError_t ee = cudaSuccess;
+    if (gi >= 2) ee = cudaStreamWaitEvent(op->copy_stream, op->ev_free[b], 0);
+    if (ee == cudaSuccess)
+      ee = cudaMemcpy2DAsync(op->ws_stage[b].ptr, (size_t)kv * n * ce, static_cast<const char*>(in) + (size_t)a0 * n * ce,
+                             (size_t)k * n * ce, (size_t)kv * n * ce, op->n_omega, cudaMemcpyHostToDevice,
+                             op->copy_stream);
+    if (ee == cudaSuccess) ee = cudaEventRecord(op->ev_copied[b], op->copy_stream);
+    return ee;
+  };
+  if (host_in && (e = stage_copy(0)) != cudaSuccess) return cuda_fail(e, "staging copy");
   for (int v0 = 0; v0 < (trial ? std::min(kg, k) : k); v0 += kg) {
     const int kv = std::min(kg, k - v0);
     const int64_t rows = (int64_t)kv * n;
@@ -656,6 +693,13 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
     int synth_stride = 1;
     const void* gin = static_cast<const char*>(in) + (size_t)v0 * n * ce;
     int64_t gin_stride = (int64_t)k * n;
+    const int gi = v0 / kg;
+    if (host_in) {   // next group's copy first, then wait for this group's
+      if (v0 + kg < k && (e = stage_copy(gi + 1)) != cudaSuccess) return cuda_fail(e, "staging copy");
+      if ((e = cudaStreamWaitEvent(stream, op->ev_copied[gi & 1], 0)) != cudaSuccess) return cuda_fail(e, "staging wait");
+      gin = op->ws_stage[gi & 1].ptr;
+      gin_stride = rows;
+    }
     if (s_in) {   // the group's coefficients times the input scaling (B, or C W_y for the adjoint)
       if ((st = ensure(op->ws_scaled, (size_t)op->n_omega * rows * ce)) != RSV_OK) return st;
       ProfScope ps(op, PROF_GLUE);
@@ -734,6 +778,8 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
         if (n_end >= sc.forced && small) break;
       }
     }
+    if (host_in && (e = cudaEventRecord(op->ev_free[gi & 1], stream)) != cudaSuccess)
+      return cuda_fail(e, "staging event");
     if (trial) {
       float ms = 0.f;
       e = cudaEventRecord(ev1, stream);
@@ -800,12 +846,13 @@ static rsv_status autotune_impl(rsv_operator op, const void* in, int k, const rs
 }
 
 rsv_status march_any(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out, bool adjoint,
-                     int scaling) {
+                     int scaling, bool host_in) {
   if (!op || !in || !out || k < 1) return fail(RSV_ERR_INVALID_ARG, "bad march arguments");
   if (!op->have_freq) return fail(RSV_ERR_STATE, "rsv_set_frequencies must come first");
   if (in == out) return fail(RSV_ERR_INVALID_ARG, "input and output blocks must not alias");
-  return op->prec == RSV_PREC_FP64 ? march_impl<double>(op, in, k, opts, out, adjoint, scaling)
-                                   : march_impl<float>(op, in, k, opts, out, adjoint, scaling);
+  if (opts && opts->group_vectors < 0) return fail(RSV_ERR_INVALID_ARG, "group_vectors must be >= 0");
+  return op->prec == RSV_PREC_FP64 ? march_impl<double>(op, in, k, opts, out, adjoint, scaling, nullptr, host_in)
+                                   : march_impl<float>(op, in, k, opts, out, adjoint, scaling, nullptr, host_in);
 }
 
 }  // namespace rsv
@@ -818,6 +865,16 @@ extern "C" rsv_status rsv_march_direct(rsv_operator op, const void* f_hat, int32
 extern "C" rsv_status rsv_march_adjoint(rsv_operator op, const void* y_hat, int32_t k, const rsv_march_opts* opts,
                                         void* w_hat) {
   return march_any(op, y_hat, k, opts, w_hat, true, SCALE_PLAIN);
+}
+
+extern "C" rsv_status rsv_march_direct_host(rsv_operator op, const void* f_hat_host, int32_t k,
+                                            const rsv_march_opts* opts, void* y_hat) {
+  return march_any(op, f_hat_host, k, opts, y_hat, false, SCALE_PLAIN, true);
+}
+
+extern "C" rsv_status rsv_march_adjoint_host(rsv_operator op, const void* y_hat_host, int32_t k,
+                                             const rsv_march_opts* opts, void* w_hat) {
+  return march_any(op, y_hat_host, k, opts, w_hat, true, SCALE_PLAIN, true);
 }
 
 // Diagonal B, C, W_f, W_y (Sec. 2.1).  The per-point factors the runs use are formed here in FP64.

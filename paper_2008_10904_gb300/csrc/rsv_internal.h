@@ -201,6 +201,11 @@ struct rsv_operator_s {
   std::vector<rsv::TileGraph> tile_graphs;
   cudaStream_t cap_stream = nullptr;
   int64_t graph_replays = 0;
+  // host-input marches: two device staging buffers of one vector group's coefficients, the copy
+  // stream, and events (copy done / buffer free) per staging buffer
+  rsv::Workspace ws_stage[2];
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   // autotuned tile length and vector group (rsv_autotune) for marches of tuned_k vectors
   int tuned_k = 0, tuned_tile = 0, tuned_group = 0;
   int64_t last_steps = 0;              // steps marched by the latest march's last vector group
@@ -227,7 +232,7 @@ enum { PROF_SYNTH = 0, PROF_MARCH = 1, PROF_ANALYSIS = 2, PROF_GLUE = 3 };
 // or the runs of W_y^{1/2} C R B W_f^{-1/2} and its conjugate transpose
 enum { SCALE_NONE = 0, SCALE_PLAIN = 1, SCALE_TILDE = 2 };
 rsv_status march_any(rsv_operator op, const void* in, int k, const rsv_march_opts* opts, void* out, bool adjoint,
-                     int scaling);
+                     int scaling, bool host_in = false);
 
 // ----- launchers (contract_kernels.cu) -------------------------------------
 struct TileGeom {

@@ -52,7 +52,7 @@ class rsv_operator_desc(ctypes.Structure):
 
 class rsv_march_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("n_transient_windows", ctypes.c_int32),
-                ("tail_steps", ctypes.c_int64), ("tile_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tail_steps", ctypes.c_int64), ("tile_steps", ctypes.c_int32), ("group_vectors", ctypes.c_int32),
                 ("tail_tol", ctypes.c_double), ("decay_tol", ctypes.c_double), ("decay_max_steps", ctypes.c_int64),
                 ("decay_seed", ctypes.c_uint64)]
 
@@ -82,6 +82,10 @@ _ENTRY_POINTS = {
                                         ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
     "rsv_march_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
+    "rsv_march_direct_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
+    "rsv_march_adjoint_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                              ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
     "rsv_march_direct_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                ctypes.POINTER(rsv_march_opts), ctypes.c_void_p]),
     "rsv_gains_modes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
@@ -170,10 +174,23 @@ def _ptr(x) -> int:
 
 
 def _opts(variant="ssrm", n_transient_windows=0, tail_steps=0, tile_steps=0, tail_tol=0.0, decay_tol=0.0,
-          decay_max_steps=0, decay_seed=0):
+          decay_max_steps=0, decay_seed=0, group_vectors=0):
     return rsv_march_opts(RSV_SSRM if variant == "ssrm" else RSV_TRM, int(n_transient_windows),
-                          int(tail_steps), int(tile_steps), 0, float(tail_tol), float(decay_tol),
+                          int(tail_steps), int(tile_steps), int(group_vectors), float(tail_tol), float(decay_tol),
                           int(decay_max_steps), int(decay_seed))
+
+
+def _host_ptr(x) -> int:
+    """Address of a host buffer: a CPU torch tensor (pinned for asynchronous copies) or a numpy array."""
+    if hasattr(x, "data_ptr"):
+        if x.is_cuda or not x.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("host buffers must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(type(x))
 
 
 class Operator:
@@ -231,6 +248,17 @@ def rsv_march_direct(op: Operator, f_hat, k: int, y_hat, **opts):
 def rsv_march_adjoint(op: Operator, y_hat, k: int, w_hat, **opts):
     o = _opts(**opts)
     _check(_lib.rsv_march_adjoint(op.handle, _ptr(y_hat), int(k), ctypes.byref(o), _ptr(w_hat)))
+
+
+def rsv_march_direct_host(op: Operator, f_hat_host, k: int, y_hat, **opts):
+    """Direct march of a host input block (copies overlapped with the march, per vector group)."""
+    o = _opts(**opts)
+    _check(_lib.rsv_march_direct_host(op.handle, _host_ptr(f_hat_host), int(k), ctypes.byref(o), _ptr(y_hat)))
+
+
+def rsv_march_adjoint_host(op: Operator, y_hat_host, k: int, w_hat, **opts):
+    o = _opts(**opts)
+    _check(_lib.rsv_march_adjoint_host(op.handle, _host_ptr(y_hat_host), int(k), ctypes.byref(o), _ptr(w_hat)))
 
 
 def rsv_march_direct_static(op: Operator, f_hat, k: int, y_hat, **opts):

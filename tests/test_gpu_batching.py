@@ -164,3 +164,48 @@ def test_autotune_choice_is_used_and_exact(rsv, make, prec):
         assert err < (TOL64 if prec == 0 else TOL32), err
     finally:
         rsv.rsv_destroy_operator(op)
+
+
+def _gl_small_k5():
+    sysm = W.GL1D(n=(96,), mu0=(-0.1,))
+    return W.Workload("gl_host", sysm, np.linspace(-1.0, 1.0, 6), 0.02, 5, "ssrm", n_transient_windows=1,
+                      seed=W.SEED_BASE + 74)
+
+
+@pytest.mark.parametrize("make,prec", [(_gl_small_k5, 0), (_gl_small_k5, 1), (lambda: _adr(k=5), 1),
+                                       (lambda: _adv(k=5), 1)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_host_input_march_overlaps_and_matches(rsv, make, prec, adjoint):
+    """Host-input march in groups of 2 vectors (groups 2, 2, 1: the staging buffers are refilled) =
+    the device-input march, bit for bit, for pinned and pageable input; grouping does not change
+    any vector's result; and the result matches the oracle."""
+    import torch
+    w = make()
+    real = w.real_state
+    op = rsv.create_for_workload(w, prec)
+    try:
+        fh = W.test_block(w)
+        if prec == 1:
+            fh = fh.astype(np.complex64).astype(np.complex128)
+        x = _dev(fh, prec)
+        y_dev = torch.empty_like(x)
+        y_grp = torch.empty_like(x)
+        y_pin = torch.empty_like(x)
+        y_pag = torch.empty_like(x)
+        opts = rsv.march_opts_for(w)
+        f_dev = rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct
+        f_host = rsv.rsv_march_adjoint_host if adjoint else rsv.rsv_march_direct_host
+        f_dev(op, x, w.k, y_dev, **opts)
+        f_dev(op, x, w.k, y_grp, group_vectors=2, **opts)
+        assert "group=2" in rsv.rsv_describe(op)
+        pinned = x.cpu().pin_memory()
+        f_host(op, pinned, w.k, y_pin, group_vectors=2, **opts)
+        f_host(op, x.cpu().numpy(), w.k, y_pag, group_vectors=2, **opts)
+        assert torch.equal(y_dev, y_grp) and torch.equal(y_dev, y_pin) and torch.equal(y_dev, y_pag)
+        g = frequencies.make_grid(w.omegas, w.dt)
+        a = operators.gl1d(w.system) if not real else _matrix(w)
+        ref = march.march(a, g, fh, variant="ssrm", n_trans=w.n_transient_windows, adjoint=adjoint, real_state=real)
+        err = rel_rows(y_dev.cpu().numpy().astype(np.complex128), ref)
+        assert err < (TOL64 if prec == 0 else TOL32), err
+    finally:
+        rsv.rsv_destroy_operator(op)
