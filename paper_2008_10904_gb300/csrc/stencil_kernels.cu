@@ -935,11 +935,39 @@ __device__ __forceinline__ float sponge_fast(int gi, int gj, const StGeom& g, fl
   return (float)g.sponge_amp * t * t;
 }
 
-// Requires nx % 4 == 0 (16-byte rows of the input tile and of the second stage's float4 accesses).
+// Shared-memory tiles of the 2-D pair kernel (floats): the stencil input (rows Y0-2 .. Y0+33, x from
+// X0-4, 72 wide), the first stage's forcing and (pair B) state on its halo region (rows Y0-1 ..
+// Y0+32, 72 wide), the first-stage result (66 x 34), and the second stage's forcing and (pair B)
+// accumulator on the tile (64 x 32).  Every global read of the kernel is one of these 16-byte
+// asynchronous copies, issued together at the start.
+constexpr int k2HW = k2UW, k2HH = k2XH;            // halo-region tiles: 72 x 34
+constexpr int k2Smem = (k2UH * k2UW + 2 * k2HH * k2HW + k2XH * k2XW + 2 * k2TX * k2TY) * 4;
+
+// Copies rows [y0, y0 + nrow) x [x0, x0 + 4 nch) of a field into a tile with rows of width w (16-byte
+// chunks, wholly inside the grid or zero).
+__device__ __forceinline__ void tile_copy(float* t, int w, const float* src, int x0, int nch, int y0, int nrow,
+                                          int nx, int ny, int tid) {
+  for (int e = tid; e < nrow * nch; e += k2Threads) {
+    const int ly = e / nch, ch = e - ly * nch;
+    const int gj = y0 + ly, gx = x0 + 4 * ch;
+    float* d = t + ly * w + 4 * ch;
+    if (src != nullptr && gj >= 0 && gj < ny && gx >= 0 && gx < nx)
+      cp_async16(d, src + (int64_t)gj * nx + gx);
+    else
+      *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Requires nx % 4 == 0 (16-byte rows of the tiles and of the second stage's float4 stores).
 template <bool PAIR_B>
 __global__ void __launch_bounds__(k2Threads) adr2d_pair_kernel(StGeom g, Pair3D P) {
-  __shared__ __align__(16) float tin[k2UH * k2UW];
-  __shared__ float mid[k2XH * k2XW];
+  extern __shared__ __align__(16) unsigned char smem2[];
+  float* tin = reinterpret_cast<float*>(smem2);        // [k2UH][k2UW]
+  float* ta = tin + k2UH * k2UW;                        // [k2HH][k2HW] forcing of the first stage
+  float* tu = ta + k2HH * k2HW;                         // [k2HH][k2HW] pair B: the state u
+  float* mid = tu + k2HH * k2HW;                        // [k2XH][k2XW]
+  float* tb = mid + k2XH * k2XW;                        // [k2TY][k2TX] forcing of the second stage
+  float* tc = tb + k2TX * k2TY;                         // [k2TY][k2TX] pair B: the accumulator
   __shared__ float rowc[k2XH][3];            // per row of the first-stage tile: cw, ce, diagonal without sponge
   const int nx = g.nx, ny = g.ny;
   int b = blockIdx.x;
@@ -948,11 +976,6 @@ __global__ void __launch_bounds__(k2Threads) adr2d_pair_kernel(StGeom g, Pair3D 
   const int ntx = (nx + k2TX - 1) / k2TX;
   const int X0 = (b % ntx) * k2TX, Y0 = (b / ntx) * k2TY;
   const int64_t base = (int64_t)v * g.n;
-  const float* __restrict__ in = P.in + base;
-  const float* __restrict__ fa = P.fa ? P.fa + base : nullptr;
-  const float* __restrict__ fb = P.fb ? P.fb + base : nullptr;
-  const float* __restrict__ pu = PAIR_B ? P.u + base : nullptr;
-  const float* __restrict__ pacc = PAIR_B ? P.acc + base : nullptr;
   float* __restrict__ out = P.out + base;
   float* __restrict__ acc_out = PAIR_B ? nullptr : P.acc_out + base;
   float* __restrict__ ysnap = P.ysnap ? P.ysnap + base : nullptr;
@@ -967,16 +990,11 @@ __global__ void __launch_bounds__(k2Threads) adr2d_pair_kernel(StGeom g, Pair3D 
   const float c1 = PAIR_B ? h : 0.5f * h;
   const float c2 = PAIR_B ? h / 6.f : 0.5f * h;
   const int tid = threadIdx.x;
-  // the pair's stencil input with a two-cell halo; 16-byte chunks lie wholly inside or outside
-  for (int e = tid; e < k2UH * k2Row4; e += k2Threads) {
-    const int ly = e / k2Row4, ch = e - ly * k2Row4;
-    const int gj = Y0 - 2 + ly, gx = X0 - 4 + 4 * ch;
-    float* d = tin + ly * k2UW + 4 * ch;
-    if (gj >= 0 && gj < ny && gx >= 0 && gx < nx)
-      cp_async16(d, in + (int64_t)gj * nx + gx);
-    else
-      *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
+  tile_copy(tin, k2UW, P.in + base, X0 - 4, k2UW / 4, Y0 - 2, k2UH, nx, ny, tid);
+  tile_copy(ta, k2HW, P.fa ? P.fa + base : nullptr, X0 - 4, k2HW / 4, Y0 - 1, k2HH, nx, ny, tid);
+  if (PAIR_B) tile_copy(tu, k2HW, P.u + base, X0 - 4, k2HW / 4, Y0 - 1, k2HH, nx, ny, tid);
+  tile_copy(tb, k2TX, P.fb ? P.fb + base : nullptr, X0, k2TX / 4, Y0, k2TY, nx, ny, tid);
+  if (PAIR_B) tile_copy(tc, k2TX, P.acc + base, X0, k2TX / 4, Y0, k2TY, nx, ny, tid);
   asm volatile("cp.async.commit_group;" ::: "memory");
   if (tid < k2XH) {   // row coefficients of rows Y0 - 1 .. Y0 + k2TY
     const int gj = min(max(Y0 - 1 + tid, 0), ny - 1);
@@ -996,17 +1014,17 @@ __global__ void __launch_bounds__(k2Threads) adr2d_pair_kernel(StGeom g, Pair3D 
     float xo = 0.f;
     if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
       const int et = (ly + 1) * k2UW + lx + 3;      // tin index of (gi, gj)
-      const int64_t q = (int64_t)gj * nx + gi;
+      const int eh = ly * k2HW + lx + 3;            // halo-region tile index of (gi, gj)
       const float cc = rowc[ly][2] - (near_wall ? sponge_fast(gi, gj, g, inv_s) : 0.f);
       const float k = rowc[ly][0] * tin[et - 1] + rowc[ly][1] * tin[et + 1] + cy * (tin[et - k2UW] + tin[et + k2UW]) +
-                      cc * tin[et] + (fa ? fa[q] : 0.f);
-      const float uu = PAIR_B ? pu[q] : tin[et];
+                      cc * tin[et] + ta[eh];
+      const float uu = PAIR_B ? tu[eh] : tin[et];
       xo = uu + c1 * k;
     }
     mid[e] = xo;
   }
   __syncthreads();
-  // second stage on the tile, four cells along x per item (16-byte global accesses)
+  // second stage on the tile, four cells along x per item (16-byte stores)
   for (int e = tid; e < k2TX * k2TY / 4; e += k2Threads) {
     const int tx = 4 * (e % (k2TX / 4)), ty = e / (k2TX / 4);
     const int gi0 = X0 + tx, gj = Y0 + ty;
@@ -1014,14 +1032,13 @@ __global__ void __launch_bounds__(k2Threads) adr2d_pair_kernel(StGeom g, Pair3D 
     const int64_t q = (int64_t)gj * nx + gi0;
     const int ly = ty + 1;                          // row of the first-stage tile
     const float cw = rowc[ly][0], ce = rowc[ly][1], cd = rowc[ly][2];
-    const float4 f4 = fb ? ld4(fb + q) : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 kk, xm;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int em = ly * k2XW + tx + c + 1;
       const float cc = cd - (near_wall ? sponge_fast(gi0 + c, gj, g, inv_s) : 0.f);
       const float k = cw * mid[em - 1] + ce * mid[em + 1] + cy * (mid[em - k2XW] + mid[em + k2XW]) + cc * mid[em] +
-                      get4(f4, c);
+                      tb[ty * k2TX + tx + c];
       set4(kk, c, k);
       set4(xm, c, mid[em]);
     }
@@ -1039,13 +1056,13 @@ __global__ void __launch_bounds__(k2Threads) adr2d_pair_kernel(StGeom g, Pair3D 
       st4(acc_out + q, oa);
       if (ysnap) st4(ysnap + q, uu);
     } else {
-      const float4 uu = ld4(pu + q), a4 = ld4(pacc + q);
+      const float* urow = tu + (ty + 1) * k2HW + tx + 4;
       float4 o;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const float u1 = get4(uu, c);
-        const float a = get4(a4, c) + (get4(xm, c) - u1) * (1.f / 3.f);    // + h/3 k3
-        set4(o, c, a + c2 * get4(kk, c));                                    // + h/6 k4
+        const float u1 = urow[c];
+        const float a = tc[ty * k2TX + tx + c] + (get4(xm, c) - u1) * (1.f / 3.f);   // + h/3 k3
+        set4(o, c, a + c2 * get4(kk, c));                                           // + h/6 k4
       }
       st4(out + q, o);
     }
@@ -1054,8 +1071,11 @@ __global__ void __launch_bounds__(k2Threads) adr2d_pair_kernel(StGeom g, Pair3D 
 
 template <bool PAIR_B>
 cudaError_t launch_pair2d(rsv_operator op, const StGeom& g, const Pair3D& P) {
+  // per-device attribute: set before every launch (cheap next to a pass over the field)
+  cudaError_t e = cudaFuncSetAttribute(adr2d_pair_kernel<PAIR_B>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2Smem);
+  if (e != cudaSuccess) return e;
   const unsigned ntx = (unsigned)((g.nx + k2TX - 1) / k2TX), nty = (unsigned)((g.ny + k2TY - 1) / k2TY);
-  adr2d_pair_kernel<PAIR_B><<<ntx * nty * (unsigned)g.kg, k2Threads, 0, op->stream>>>(g, P);
+  adr2d_pair_kernel<PAIR_B><<<ntx * nty * (unsigned)g.kg, k2Threads, k2Smem, op->stream>>>(g, P);
   return cudaGetLastError();
 }
 
