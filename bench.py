@@ -211,20 +211,13 @@ def load_peaks():
 # category, tile steps, rows per launch).  An entry is dropped whenever the kernel it
 # describes changes.  Sources (summaries in profiles/):
 #   dense march  dense_tc_march_c2.txt: one 256-step launch, 84.35 MB read + 24.63 MB written
-#   1-D march    gl1d_tile_c5.txt: one 127-step launch, 754.9 MB read + 344.4 MB written
-#   2-D march    adr2d_stage_c3.txt: the four stage kernels of one step at 16 vectors,
-#                558.5 MB per step, scaled by 255 steps (traffic per step is constant)
 #   3-D march    adv3d_pair_c4.txt: the two stage-pair kernels of one step at 2 vectors,
-#                1348.4 MB per step, scaled by 255 steps
+#                1347.2 MB per step, scaled by 255 steps (traffic per step is constant)
 TRAFFIC = {
     ("dense_hermite_gl_n1024_k32_w256_trm", "march", 256, 32768):
         {"bytes": 108.98e6, "src": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"},
-    ("gl_batch64_k8_w64_ssrm", "march", 127, 365184):
-        {"bytes": 1.0993e9, "src": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"},
-    ("adr2d_1024x512_k16_w128_ssrm", "march", 255, 8388608):
-        {"bytes": 255 * 558.5e6, "src": "ncu dram bytes of the four stage kernels of one step x 255 steps"},
     ("adv3d_256x128x128x3_k8_w64_ssrm", "march", 255, 25165824):
-        {"bytes": 255 * 1348.4e6, "src": "ncu dram bytes of the two stage-pair kernels of one step x 255 steps"},
+        {"bytes": 255 * 1347.2e6, "src": "ncu dram bytes of the two stage-pair kernels of one step x 255 steps"},
 }
 
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
