@@ -27,6 +27,28 @@ from __future__ import annotations
 
 import numpy as np
 
+from .decay import splitmix64
+
+
+def gaussian_test_block(seed: int, n_omega: int, k: int, n: int, real_rows=()) -> np.ndarray:
+    """Seeded Gaussian test block Omega [n_omega][k][n] complex128 that the seeded randomized SVD
+    draws: entry e (row-major over the block) takes the SplitMix64 values 2e and 2e + 1 of stream
+    `seed` (top 53 bits: u1 = (x + 1) 2^-53 in (0, 1], u2 = x 2^-53 in [0, 1)) through the Box-Muller
+    transform (Box & Muller 1958), z0 + i z1 = sqrt(-2 ln u1) exp(2 pi i u2); the entry is
+    (z0 + i z1) / sqrt(2), and in the rows listed in `real_rows` (the w = 0 row of a real system)
+    the real N(0, 1) value z0."""
+    count = n_omega * k * n
+    x = splitmix64(seed, 2 * count) >> np.uint64(11)
+    u1 = (x[0::2].astype(np.float64) + 1.0) * 2.0 ** -53
+    u2 = x[1::2].astype(np.float64) * 2.0 ** -53
+    r = np.sqrt(-2.0 * np.log(u1))
+    z0 = r * np.cos(2.0 * np.pi * u2)
+    z1 = r * np.sin(2.0 * np.pi * u2)
+    out = ((z0 + 1j * z1) / np.sqrt(2.0)).reshape(n_omega, k, n)
+    for j in real_rows:
+        out[j] = z0.reshape(n_omega, k, n)[j]
+    return out
+
 
 def qr_positive(y):
     """Thin QR of y (n x k) with a positive real diagonal in R (unique form)."""

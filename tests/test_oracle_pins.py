@@ -306,3 +306,25 @@ def test_trm_check_points_every_step_by_default():
     for y in (y1, y64):
         assert np.abs(y - ref).max() / np.abs(ref).max() < tol
     assert np.abs(y64 - y1).max() / np.abs(ref).max() < tol
+
+
+def test_seeded_gaussian_block_distribution():
+    """The seeded test block is standard complex Gaussian ((N(0,1) + i N(0,1)) / sqrt 2 per entry;
+    N(0,1) in real rows): moments, independence of the two parts and a Kolmogorov-Smirnov test
+    against the normal distribution; the same seed gives the same block, another seed another."""
+    from scipy import stats
+    from oracle import rsvd
+    b = rsvd.gaussian_test_block(77, 3, 4, 5000, real_rows=(0,))
+    assert b.shape == (3, 4, 5000)
+    c = b[1:].ravel()
+    m = c.size
+    assert abs(c.real.mean()) < 5 * np.sqrt(0.5 / m) and abs(c.imag.mean()) < 5 * np.sqrt(0.5 / m)
+    assert abs(c.real.var() - 0.5) < 0.02 and abs(c.imag.var() - 0.5) < 0.02
+    assert abs(np.corrcoef(c.real, c.imag)[0, 1]) < 5 / np.sqrt(m)
+    assert stats.kstest(c.real * np.sqrt(2.0), "norm").pvalue > 1e-3
+    assert stats.kstest(c.imag * np.sqrt(2.0), "norm").pvalue > 1e-3
+    r = b[0].ravel()
+    assert not r.imag.any() and abs(r.real.var() - 1.0) < 0.05
+    assert stats.kstest(r.real, "norm").pvalue > 1e-3
+    assert np.array_equal(b, rsvd.gaussian_test_block(77, 3, 4, 5000, real_rows=(0,)))
+    assert not np.allclose(b, rsvd.gaussian_test_block(78, 3, 4, 5000, real_rows=(0,)))
