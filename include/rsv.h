@@ -272,6 +272,18 @@ rsv_status rsv_gains_modes(rsv_operator op, const void* omega_block, int32_t k, 
                            int32_t n_modes, const rsv_march_opts* opts, double* gains, void* forcing_modes,
                            void* response_modes);
 
+/* rsv_gains_modes with the test block drawn by the library from a seed: entry
+ * e of the [n_omega][k][n] block (row-major) takes the values 2e and 2e + 1 of
+ * the SplitMix64 stream `seed` (Steele, Lea & Flood 2014; top 53 bits:
+ * u1 = (x + 1) 2^-53, u2 = x 2^-53) through the Box-Muller transform, giving
+ * (z0 + i z1) / sqrt(2) with z0 + i z1 = sqrt(-2 ln u1) exp(2 pi i u2); for a
+ * real-state operator the w = 0 row holds the real N(0, 1) values z0.  The
+ * block lives in a library workspace.  Other arguments and errors as for
+ * rsv_gains_modes. */
+rsv_status rsv_gains_modes_seeded(rsv_operator op, int32_t k, int32_t n_power_iter, int32_t n_modes, uint64_t seed,
+                                  const rsv_march_opts* opts, double* gains, void* forcing_modes,
+                                  void* response_modes);
+
 /* Rayleigh-Ritz refinement on a given forcing basis (App. A: gains and modes
  * estimated from the eigen-decomposition of R^H R projected onto a subspace).
  * With Q the orthonormalised basis (CholeskyQR2 per frequency and instance),

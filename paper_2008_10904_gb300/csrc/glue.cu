@@ -449,6 +449,60 @@ extern "C" rsv_status rsv_orthonormalize(rsv_operator op, void* block, int32_t k
   return op->prec == RSV_PREC_FP64 ? orthonormalize<double>(op, block, k, r) : orthonormalize<float>(op, block, k, r);
 }
 
+namespace rsv {
+namespace {
+__device__ __forceinline__ uint64_t splitmix64_value(uint64_t seed, uint64_t i) {   // value i of stream seed
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Entry e of the seeded test block: SplitMix64 values 2e, 2e + 1 through the Box-Muller transform,
+// (z0 + i z1) / sqrt 2, or z0 in the w = 0 row of a real-state operator (row_real).
+template <typename R>
+__global__ void gaussian_block_kernel(cpx<R>* __restrict__ out, int64_t count, int64_t row_len, int row_real,
+                                      uint64_t seed) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const double u1 = (double)((splitmix64_value(seed, 2 * (uint64_t)e) >> 11) + 1ull) * 0x1.0p-53;
+    const double u2 = (double)(splitmix64_value(seed, 2 * (uint64_t)e + 1) >> 11) * 0x1.0p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    const bool real_row = row_real >= 0 && e / row_len == row_real;
+    const double s = real_row ? 1.0 : 0.70710678118654752440;
+    out[e] = mk<R>((R)(s * r * cs), real_row ? R(0) : (R)(s * r * sn));
+  }
+}
+}  // namespace
+}  // namespace rsv
+
+extern "C" rsv_status rsv_gains_modes_seeded(rsv_operator op, int32_t k, int32_t n_power_iter, int32_t n_modes,
+                                             uint64_t seed, const rsv_march_opts* opts, double* gains, void* fmodes,
+                                             void* rmodes) {
+  if (!op || !gains) return fail(RSV_ERR_INVALID_ARG, "null argument");
+  if (!op->have_freq) return fail(RSV_ERR_STATE, "rsv_set_frequencies must come first");
+  if (k < 1 || k > 32) return fail(RSV_ERR_INVALID_ARG, "k must be 1..32");
+  const int64_t count = (int64_t)op->n_omega * k * op->n;
+  const size_t eb = op->prec == RSV_PREC_FP64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+  rsv_status s = ensure(op->ws_omega, (size_t)count * eb);
+  if (s != RSV_OK) return s;
+  int row_real = -1;   // the w = 0 row of a real-state operator carries real test vectors
+  if (op->real_state)
+    for (int j = 0; j < op->n_omega; ++j)
+      if (op->pj[j] == 0) row_real = j;
+  const unsigned blocks = (unsigned)std::min<int64_t>((count + 255) / 256, 16 * std::max(op->sm_count, 1));
+  if (op->prec == RSV_PREC_FP64)
+    gaussian_block_kernel<double><<<blocks, 256, 0, op->stream>>>((cpx<double>*)op->ws_omega.ptr, count,
+                                                                  (int64_t)k * op->n, row_real, seed);
+  else
+    gaussian_block_kernel<float><<<blocks, 256, 0, op->stream>>>((cpx<float>*)op->ws_omega.ptr, count,
+                                                                 (int64_t)k * op->n, row_real, seed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "seeded test block");
+  return rsv_gains_modes(op, op->ws_omega.ptr, k, n_power_iter, n_modes, opts, gains, fmodes, rmodes);
+}
+
 extern "C" rsv_status rsv_gains_modes(rsv_operator op, const void* omega_block, int32_t k, int32_t n_power_iter,
                                       int32_t n_modes, const rsv_march_opts* opts, double* gains, void* fmodes,
                                       void* rmodes) {

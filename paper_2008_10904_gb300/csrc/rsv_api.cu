@@ -130,6 +130,7 @@ rsv_operator_s::~rsv_operator_s() {
   for (rsv::TileGraph& g : tile_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (ws_omega.ptr) cudaFree(ws_omega.ptr);
   for (int i = 0; i < 2; ++i) {
     if (ws_stage[i].ptr) cudaFree(ws_stage[i].ptr);
     if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);

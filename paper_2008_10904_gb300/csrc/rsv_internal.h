@@ -204,6 +204,7 @@ struct rsv_operator_s {
   // host-input marches: two device staging buffers of one vector group's coefficients, the copy
   // stream, and events (copy done / buffer free) per staging buffer
   rsv::Workspace ws_stage[2];
+  rsv::Workspace ws_omega;               // the seeded randomized SVD's test block
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   // autotuned tile length and vector group (rsv_autotune) for marches of tuned_k vectors

@@ -91,6 +91,9 @@ _ENTRY_POINTS = {
     "rsv_gains_modes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.POINTER(rsv_march_opts),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p]),
+    "rsv_gains_modes_seeded": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_uint64, ctypes.POINTER(rsv_march_opts),
+                                              ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p]),
     "rsv_set_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -276,6 +279,18 @@ def rsv_gains_modes(op: Operator, omega_block, k: int, n_power_iter: int, n_mode
     _check(_lib.rsv_gains_modes(op.handle, _ptr(omega_block), int(k), int(n_power_iter), int(n_modes),
                                 ctypes.byref(o), gains.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                 _ptr(forcing_modes), _ptr(response_modes)))
+    return gains
+
+
+def rsv_gains_modes_seeded(op: Operator, k: int, n_power_iter: int, n_modes: int, seed: int, gains: np.ndarray,
+                           forcing_modes=None, response_modes=None, **opts):
+    """Randomized SVD from a library-drawn seeded Gaussian test block; gains filled in place."""
+    if gains.dtype != np.float64 or not gains.flags.c_contiguous:
+        raise ValueError("gains must be a C-contiguous float64 array")
+    o = _opts(**opts)
+    _check(_lib.rsv_gains_modes_seeded(op.handle, int(k), int(n_power_iter), int(n_modes), int(seed), ctypes.byref(o),
+                                       gains.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(forcing_modes),
+                                       _ptr(response_modes)))
     return gains
 
 
