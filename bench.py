@@ -478,6 +478,34 @@ def fp64_single_vector(w, dense, stream, n_t, rank):
             "ms_per_march": per_march_ms}
 
 
+def one_frequency_march(rsv, op, w, bufs, opts, stream, step_ms):
+    """The frequencies one at a time (the cost the paper compares against, Sec. 2.4): one march of the
+    same schedule with only the first frequency (same window and steps: the grid spacing is kept),
+    timed after one untimed run, times n_omega, against the measured step (one march of all
+    frequencies and its orthonormalisation)."""
+    import torch
+    dw = float(w.omegas[1] - w.omegas[0]) if w.n_omega > 1 else 0.0
+    rsv.rsv_set_frequencies(op, w.omegas[:1], dw)
+    x1 = bufs[0][:1].contiguous()
+    y1 = torch.empty_like(x1)
+    ms = 0.0
+    for r in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rsv.rsv_march_direct(op, x1, w.k, y1, **opts)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    rsv.rsv_set_frequencies(op, w.omegas)
+    all_ms = ms * w.n_omega
+    return {"ms_per_single_frequency_march": ms, "ms_all_frequencies_one_at_a_time": all_ms,
+            "value": w.k * w.n_omega / (all_ms / 1e3), "unit": "actions/s",
+            "speedup_of_all_at_once": all_ms / step_ms,
+            "sample": f"one march of frequency {w.omegas[0]:g} alone (same window and steps, {w.k} vectors), "
+                      f"second of two runs, times {w.n_omega} frequencies"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -592,6 +620,9 @@ def run_ours(args):
         e2e_ms += e0.elapsed_time(e1)
     e2e_sec = max_over_ranks(e2e_ms / 1e3, device="cuda")
     e2e_value = job_throughput(actions_per_step(w, step_kind) * e2e_steps, ws, e2e_sec)
+    single = None
+    if step_kind == "march" and not args.no_single_frequency:
+        single = one_frequency_march(rsv, op, w, bufs, opts, stream, step_ms=total_ms / max(args.steps, 1))
     rsv.rsv_destroy_operator(op)
     del bufs, flush, pinned
     torch.cuda.empty_cache()
@@ -631,6 +662,7 @@ def run_ours(args):
         "clocks": clocks,
         "accuracy": acc,
         "fp64_single_vector": comp,
+        "one_frequency_at_a_time": single,
     }
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
@@ -676,6 +708,8 @@ def main(argv=None):
                     help="bf16: the 3-D workload's march state stored in BF16 (arithmetic in FP32)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true", help="keep the memory rule's tile and group")
+    ap.add_argument("--no-single-frequency", action="store_true",
+                    help="skip the one-frequency-at-a-time comparison march")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement (<= --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
