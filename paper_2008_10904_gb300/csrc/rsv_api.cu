@@ -653,6 +653,13 @@ static rsv_status march_impl(rsv_operator op, const void* in, int k, const rsv_m
     if (!op->copy_stream && (e = cudaStreamCreateWithFlags(&op->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
       return cuda_fail(e, "copy stream");
   }
+  // whatever path the march leaves by, no copy from the caller's host block is left in flight
+  struct CopyDrain {
+    cudaStream_t s;
+    ~CopyDrain() {
+      if (s) cudaStreamSynchronize(s);
+    }
+  } copy_drain{host_in ? op->copy_stream : nullptr};
   auto stage_copy = [&](int gi) -> cudaError_t {   // group gi into staging buffer gi % 2
     const int a0 = gi * kg;
     const int kv = std::min(kg, k - a0);
