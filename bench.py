@@ -211,7 +211,8 @@ def load_peaks():
 # category, tile steps, rows per launch).  An entry is dropped whenever the kernel it
 # describes changes.  Sources (summaries in profiles/):
 #   dense march  dense_tc_march_c2.txt: one 256-step launch, 84.35 MB read + 24.63 MB written
-#   1-D march    gl1d_pack_c5.txt: one 127-step launch of the packed kernel, 1105.9 MB
+#   1-D march    gl1d_pack_c5.txt: one 127-step launch of the packed kernel (one wave of 152
+#                CTAs x 3072 slots), 750.9 MB read + 340.2 MB written
 #   2-D march    adr2d_pair_c3.txt: the two stage-pair kernels of one step at 16 vectors,
 #                342.9 MB per step, scaled by 255 steps (traffic per step is constant)
 #   3-D march    adv3d_pair_c4.txt: the two stage-pair kernels of one step at 2 vectors,
@@ -220,7 +221,7 @@ TRAFFIC = {
     ("dense_hermite_gl_n1024_k32_w256_trm", "march", 256, 32768):
         {"bytes": 108.98e6, "src": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"},
     ("gl_batch64_k8_w64_ssrm", "march", 127, 365184):
-        {"bytes": 1.1059e9, "src": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"},
+        {"bytes": 1.0911e9, "src": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"},
     ("adr2d_1024x512_k16_w128_ssrm", "march", 255, 8388608):
         {"bytes": 255 * 342.9e6, "src": "ncu dram bytes of the two stage-pair kernels of one step x 255 steps"},
     ("adv3d_256x128x128x3_k8_w64_ssrm", "march", 255, 25165824):

@@ -291,46 +291,73 @@ __global__ void __launch_bounds__(MAXT) gl1d_cn_tile_kernel(Gl1dTile t, cpx<R>* 
   }
 }
 
-// Packed RK4 tile kernel for batches of uneven instances: one CTA of PPT x blockDim slots holds
+// Packed RK4 tile kernel for batches of uneven instances: one CTA of NT threads x PPT slots holds
 // several (instance, vector) segments back to back, each followed by a zero slot, so the three-point
 // stencil of a segment's end points reads zeros exactly as at an instance's Dirichlet ends.
 // map[pack][slot] is the row (vector * n + point) of the slot's point, or -1 for a separator or an
-// unused slot.  The steps, the stage exchange and the forcing prefetch are those of
-// gl1d_tile_kernel; the divergence flag is raised per point (the march reads norms elsewhere).
-template <typename R, int PPT>
-__global__ void __launch_bounds__(1024) gl1d_pack_kernel(Gl1dTile t, const int32_t* __restrict__ map,
-                                                         cpx<R>* __restrict__ u, const cpx<R>* __restrict__ F,
-                                                         cpx<R>* __restrict__ Y, int* __restrict__ flag) {
-  extern __shared__ unsigned char smem_raw[];
-  const int cap = PPT * (int)blockDim.x;
-  const int ld = cap + 2;
+// unused slot; slot i = thread + m * NT.  The state stays in registers and each stage exchanges its
+// input through shared memory, as in gl1d_tile_kernel.  The forcing at t_n + h/2 and t_n + h is copied
+// into a shared-memory ring RING - 1 steps ahead of its use (cp.async, issued and waited for by the
+// thread that reads it, so neither registers nor a barrier are spent on it); the forcing at t_n is the
+// previous step's t_n + h value, kept in a register.  The divergence flag is raised per point (the
+// march reads norms elsewhere).
+template <typename R>
+__device__ __forceinline__ void cp_async_cpx(cpx<R>* dst, const cpx<R>* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src),
+               "n"(sizeof(cpx<R>))
+               : "memory");
+}
+
+template <typename R, int NT, int PPT, int RING>
+__global__ void __launch_bounds__(NT, 1) gl1d_pack_kernel(Gl1dTile t, const int32_t* __restrict__ map,
+                                                            cpx<R>* __restrict__ u, const cpx<R>* __restrict__ F,
+                                                            cpx<R>* __restrict__ Y, int* __restrict__ flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int cap = NT * PPT;
+  constexpr int ld = cap + 2;
   cpx<R>* sx = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][cap + 2]: zero halo, slots 1..cap, zero
+  cpx<R>* ring = sx + 2 * ld;                        // [RING][2][cap]: f(t_n + h/2), f(t_n + h)
   const cpx<R>* lo = reinterpret_cast<const cpx<R>*>(t.lo);
   const cpx<R>* di = reinterpret_cast<const cpx<R>*>(t.di);
   const cpx<R>* up = reinterpret_cast<const cpx<R>*>(t.up);
   const cpx<R> zero = mk<R>(0, 0);
-  for (int i = threadIdx.x; i < 2 * ld; i += blockDim.x) sx[i] = zero;   // separators stay zero
-  const int64_t rows = (int64_t)t.kg * t.n;
+  for (int i = threadIdx.x; i < 2 * ld; i += NT) sx[i] = zero;   // separators stay zero
+  const int rows = t.kg * (int)t.n;                               // < 2^31 (checked by the host)
+  const bool has_f = F != nullptr;
   const int32_t* pm = map + (int64_t)blockIdx.x * cap;
-  int64_t row[PPT];
-  cpx<R> cl[PPT], cd[PPT], cu[PPT], us[PPT];
-  bool ok[PPT];
+  int32_t row[PPT];
+  cpx<R> cl[PPT], cd[PPT], cu[PPT], us[PPT], f0[PPT];
 #pragma unroll
   for (int m = 0; m < PPT; ++m) {
-    const int i = threadIdx.x + m * blockDim.x;
-    const int32_t r = pm[i];
-    ok[m] = r >= 0;
+    const int32_t r = pm[threadIdx.x + m * NT];
     row[m] = r;
-    if (ok[m]) {
-      const int64_t p = r % t.n;
+    cl[m] = cd[m] = cu[m] = us[m] = f0[m] = zero;
+    if (r >= 0) {
+      const int p = r % (int)t.n;
       cl[m] = lo[p];
       cd[m] = di[p];
       cu[m] = up[p];
       us[m] = u[r];
-    } else {
-      cl[m] = cd[m] = cu[m] = us[m] = zero;
+      if (has_f && t.n0 < t.n_forced) f0[m] = F[r];
     }
   }
+  // copies of step s's forcing into ring entry s % RING, one commit group per step (empty when the
+  // step is unforced or beyond the tile, so that the group count stays one per step)
+  auto prefetch = [&](int s) {
+    if (s < t.steps && has_f && t.n0 + s < t.n_forced) {
+      cpx<R>* dst = ring + (s % RING) * 2 * cap + threadIdx.x;
+      const cpx<R>* src = F + (int64_t)(2 * s + 1) * rows;
+#pragma unroll
+      for (int m = 0; m < PPT; ++m)
+        if (row[m] >= 0) {
+          cp_async_cpx(dst + m * NT, src + row[m]);
+          cp_async_cpx(dst + cap + m * NT, src + rows + row[m]);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+#pragma unroll
+  for (int s = 0; s < RING - 1; ++s) prefetch(s);
   __syncthreads();
   const R h = R(t.h);
   const R h2 = R(0.5) * h;
@@ -340,13 +367,13 @@ __global__ void __launch_bounds__(1024) gl1d_pack_kernel(Gl1dTile t, const int32
     cpx<R>* s = sx + buf * ld;
 #pragma unroll
     for (int m = 0; m < PPT; ++m)
-      if (ok[m]) s[1 + threadIdx.x + m * blockDim.x] = x[m];
+      if (row[m] >= 0) s[1 + threadIdx.x + m * NT] = x[m];
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
-      const int i = threadIdx.x + m * blockDim.x;
+      const int i = threadIdx.x + m * NT;
       cpx<R> a = f[m];
-      if (ok[m]) {
+      if (row[m] >= 0) {
         cfma(a, cl[m], s[i]);
         cfma(a, cd[m], x[m]);
         cfma(a, cu[m], s[i + 2]);
@@ -355,69 +382,53 @@ __global__ void __launch_bounds__(1024) gl1d_pack_kernel(Gl1dTile t, const int32
     }
     buf ^= 1;
   };
-  auto load_f = [&](int s, cpx<R>* fh_out, cpx<R>* f1_out) {
-    const bool forced = (F != nullptr) && (t.n0 + s < t.n_forced);
-#pragma unroll
-    for (int m = 0; m < PPT; ++m) {
-      fh_out[m] = f1_out[m] = zero;
-      if (forced && ok[m]) {
-        fh_out[m] = F[(int64_t)(2 * s + 1) * rows + row[m]];
-        f1_out[m] = F[(int64_t)(2 * s + 2) * rows + row[m]];
-      }
-    }
-  };
-  cpx<R> f0[PPT], fh[PPT], f1[PPT], nfh[PPT], nf1[PPT];
-#pragma unroll
-  for (int m = 0; m < PPT; ++m) f0[m] = nfh[m] = nf1[m] = zero;
-  if (F != nullptr && t.n0 < t.n_forced) {
-#pragma unroll
-    for (int m = 0; m < PPT; ++m)
-      if (ok[m]) f0[m] = F[row[m]];
-  }
-  load_f(0, fh, f1);
   for (int s = 0; s < t.steps; ++s) {
-    if (s + 1 < t.steps) load_f(s + 1, nfh, nf1);
-    if (!((F != nullptr) && (t.n0 + s < t.n_forced))) {
-#pragma unroll
-      for (int m = 0; m < PPT; ++m) f0[m] = zero;
-    }
+    prefetch(s + RING - 1);   // into the entry of step s - 1, whose values are already in registers
+    asm volatile("cp.async.wait_group %0;" ::"n"(RING - 1) : "memory");   // this thread's step-s copies landed
+    const bool fs = has_f && t.n0 + s < t.n_forced;
+    const cpx<R>* rh = ring + (s % RING) * 2 * cap + threadIdx.x;
+    const cpx<R>* r1 = rh + cap;
     if (Y != nullptr && s >= t.y_first) {
 #pragma unroll
       for (int m = 0; m < PPT; ++m)
-        if (ok[m]) Y[(int64_t)s * rows + row[m]] = us[m];
+        if (row[m] >= 0) Y[(int64_t)s * rows + row[m]] = us[m];
     }
-    cpx<R> k[PPT], x[PPT], acc[PPT];
-    stage(us, f0, k);
+    cpx<R> f[PPT], k[PPT], x[PPT], acc[PPT];
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) f[m] = fs ? f0[m] : zero;
+    stage(us, f, k);
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
       acc[m] = k[m];
       x[m] = us[m] + h2 * k[m];
+      f[m] = fs ? rh[m * NT] : zero;
     }
-    stage(x, fh, k);
+    stage(x, f, k);
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
       acc[m] = acc[m] + R(2) * k[m];
       x[m] = us[m] + h2 * k[m];
+      f[m] = fs ? rh[m * NT] : zero;
     }
-    stage(x, fh, k);
+    stage(x, f, k);
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
       acc[m] = acc[m] + R(2) * k[m];
       x[m] = us[m] + h * k[m];
+      f[m] = fs ? r1[m * NT] : zero;
     }
-    stage(x, f1, k);
+    stage(x, f, k);
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
       us[m] = us[m] + h6 * (acc[m] + k[m]);
-      f0[m] = f1[m];
-      fh[m] = nfh[m];
-      f1[m] = nf1[m];
+      f0[m] = f[m];
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");   // the trailing (empty) groups
   bool bad = false;
 #pragma unroll
   for (int m = 0; m < PPT; ++m) {
-    if (ok[m]) {
+    if (row[m] >= 0) {
       u[row[m]] = us[m];
       const double q = (double)us[m].re * (double)us[m].re + (double)us[m].im * (double)us[m].im;
       bad = bad || !(q < 1e300);
@@ -479,25 +490,48 @@ cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y,
   return launch_ppt<R, 4, 1024>(t, threads, u, F, Y, norms, flag, st);
 }
 
-// Packed launch: n_packs CTAs of 1024 threads, ppt slots per thread (map from build_gl1d_packs).
+// Packed launch: n_packs CTAs of gl1d_pack_threads<R>() threads, ppt slots per thread (map from the
+// host packer).  A ring three steps deep (two ahead) unless that would not fit beside the exchange
+// buffers: ppt = 4 keeps two (one ahead).  Every variant takes at most 196.7 KB of shared memory.
+namespace {
+template <typename R, int PPT>
+struct PackCfg {
+  static constexpr int nt = gl1d_pack_threads<R>();
+  static constexpr int ring = PPT == 4 ? 2 : 3;
+  static constexpr size_t smem = sizeof(cpx<R>) * (2 * ((size_t)nt * PPT + 2) + 2 * (size_t)ring * nt * PPT);
+  static_assert(smem <= 232448, "packed GL1D kernel exceeds the shared memory of a CTA");
+};
+template <typename R, typename Fn>
+cudaError_t with_pack_kernel(int ppt, Fn&& fn) {
+  switch (ppt) {
+    case 1: return fn(gl1d_pack_kernel<R, PackCfg<R, 1>::nt, 1, PackCfg<R, 1>::ring>, PackCfg<R, 1>::smem);
+    case 2: return fn(gl1d_pack_kernel<R, PackCfg<R, 2>::nt, 2, PackCfg<R, 2>::ring>, PackCfg<R, 2>::smem);
+    case 3: return fn(gl1d_pack_kernel<R, PackCfg<R, 3>::nt, 3, PackCfg<R, 3>::ring>, PackCfg<R, 3>::smem);
+    case 4: return fn(gl1d_pack_kernel<R, PackCfg<R, 4>::nt, 4, PackCfg<R, 4>::ring>, PackCfg<R, 4>::smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
+template <typename R>
+cudaError_t gl1d_pack_occupancy(int ppt, int* ctas_per_sm) {
+  return with_pack_kernel<R>(ppt, [&](auto kernel, size_t smem) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kernel, gl1d_pack_threads<R>(), smem);
+  });
+}
+
 template <typename R>
 cudaError_t launch_gl1d_pack(const Gl1dTile& t, const int32_t* map, int n_packs, int ppt, void* u, const void* F,
                              void* Y, int* flag, cudaStream_t st) {
-  const int threads = 1024;
-  const size_t smem = sizeof(cpx<R>) * 2 * (size_t)(ppt * threads + 2);
-  auto go = [&](auto kernel) -> cudaError_t {
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    kernel<<<(unsigned)n_packs, threads, smem, st>>>(t, map, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y, flag);
+  return with_pack_kernel<R>(ppt, [&](auto kernel, size_t smem) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<(unsigned)n_packs, gl1d_pack_threads<R>(), smem, st>>>(t, map, (cpx<R>*)u, (const cpx<R>*)F,
+                                                                      (cpx<R>*)Y, flag);
     return cudaGetLastError();
-  };
-  if (ppt == 1) return go(gl1d_pack_kernel<R, 1>);
-  if (ppt == 2) return go(gl1d_pack_kernel<R, 2>);
-  if (ppt == 3) return go(gl1d_pack_kernel<R, 3>);
-  if (ppt == 4) return go(gl1d_pack_kernel<R, 4>);
-  return cudaErrorInvalidValue;
+  });
 }
 
 template <typename R>
@@ -516,6 +550,8 @@ template cudaError_t launch_gl1d_pack<double>(const Gl1dTile&, const int32_t*, i
                                              int*, cudaStream_t);
 template cudaError_t launch_gl1d_pack<float>(const Gl1dTile&, const int32_t*, int, int, void*, const void*, void*,
                                             int*, cudaStream_t);
+template cudaError_t gl1d_pack_occupancy<double>(int, int*);
+template cudaError_t gl1d_pack_occupancy<float>(int, int*);
 template cudaError_t launch_gl1d_apply<double>(const Gl1dTile&, const int32_t*, const void*, void*, cudaStream_t);
 template cudaError_t launch_gl1d_apply<float>(const Gl1dTile&, const int32_t*, const void*, void*, cudaStream_t);
 

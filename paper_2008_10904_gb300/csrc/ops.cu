@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <functional>
+#include <queue>
 #include <type_traits>
 #include <vector>
 
@@ -402,15 +404,16 @@ static Gl1dTile gl1d_geom(rsv_operator op, bool adjoint, int kg) {
 }
 
 // Packing of uneven GL1D batches: when the one-CTA-per-(instance, vector) launch needs more CTAs than
-// there are SMs, the (instance, vector) segments are packed first-fit-decreasing into CTAs of 1024
-// threads x ppt slots (each segment followed by a zero separator slot), so that short instances do
-// not hold a CTA sized for the longest one.  RSV_GL1D_PACK=0 keeps the one-per-pair launch.
+// there are SMs, the (instance, vector) segments are packed into CTAs of gl1d_pack_threads<R>() threads
+// x ppt slots (each segment followed by a zero separator slot), so that short instances do not hold a
+// CTA sized for the longest one.  RSV_GL1D_PACK=0 keeps the one-per-pair launch.
+template <typename R>
 static bool gl1d_pack_wanted(rsv_operator op, int kg) {
   static const bool env = [] {
     const char* e = getenv("RSV_GL1D_PACK");
     return !(e != nullptr && e[0] == '0');
   }();
-  return env && op->scheme == RSV_SCHEME_RK4 && op->n_inst > 1 && op->gl_max_n <= 4096 &&
+  return env && op->scheme == RSV_SCHEME_RK4 && op->n_inst > 1 && op->gl_max_n <= 4 * gl1d_pack_threads<R>() &&
          (int64_t)op->n_inst * kg > op->sm_count && (int64_t)kg * op->n < ((int64_t)1 << 31);
 }
 
@@ -419,44 +422,73 @@ struct PackItem {
   int64_t len;
   int inst, v;
 };
-// First-fit decreasing of the (instance, vector) segments into packs of cap slots.
-std::vector<std::vector<PackItem>> pack_items(const std::vector<PackItem>& items, int64_t cap) {
-  std::vector<int64_t> used;                 // slots used per pack (separators included)
-  std::vector<std::vector<PackItem>> packs;
+// Longest processing time first: the segments, longest first, each go to the least loaded of n_bins
+// packs of cap slots (a separator slot before every segment but a pack's first).  The packs of one wave
+// then carry nearly equal loads, which set the time of the wave.  Returns false when a segment finds no
+// pack with room (the least loaded has none), so the caller can add a wave.
+bool pack_lpt(const std::vector<PackItem>& items, int64_t cap, int n_bins, std::vector<std::vector<PackItem>>& packs) {
+  using Load = std::pair<int64_t, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  packs.assign((size_t)n_bins, {});
+  for (int b = 0; b < n_bins; ++b) heap.push({0, b});
   for (const PackItem& it : items) {
-    size_t b = 0;
-    for (; b < packs.size(); ++b)
-      if (used[b] + (used[b] > 0 ? 1 : 0) + it.len <= cap) break;
-    if (b == packs.size()) {
-      packs.emplace_back();
-      used.push_back(0);
-    }
-    used[b] += (used[b] > 0 ? 1 : 0) + it.len;
-    packs[b].push_back(it);
+    Load top = heap.top();
+    const int64_t need = (top.first > 0 ? 1 : 0) + it.len;
+    if (top.first + need > cap) return false;
+    heap.pop();
+    packs[(size_t)top.second].push_back(it);
+    heap.push({top.first + need, top.second});
   }
-  return packs;
+  packs.erase(std::remove_if(packs.begin(), packs.end(), [](const std::vector<PackItem>& p) { return p.empty(); }),
+              packs.end());
+  return true;
 }
 }  // namespace
 
-// Slots per thread: the fewest that hold the longest instance.  More slots per thread (fewer CTAs,
-// down to one wave of one 1024-thread CTA per SM) measured slower on the 64-instance batch (3 slots:
-// 679 ms against 581 ms for 2 slots in two waves; the kernel is bound by per-SM issue and barrier
-// latency, not by the number of waves), so they are used only when RSV_GL1D_PPT forces them.
+// Slots per thread (ppt, 1 to 4, at least enough for the longest instance): the one whose packs fill
+// the fewest waves (SMs x resident CTAs), the smaller on a tie.  Each wave costs about the time of its
+// fullest pack, so one wave of CTAs holding ~2400 of 3072 slots beats two of ~1200 of 2048 (0.29
+// against 0.38 ms per 127-step tile on the 64-instance batch, where the fixed per-warp work of a step
+// is spread over fewer slots).  For each ppt the fill takes as many waves as the slots need, one more
+// while the longest-first fill leaves a segment without room.  RSV_GL1D_PPT forces a ppt.
+template <typename R>
 static cudaError_t gl1d_build_packs(rsv_operator op, int kg) {
   if (op->pack_map != nullptr && op->pack_kg == kg) return cudaSuccess;
+  const int nt = gl1d_pack_threads<R>();
   std::vector<PackItem> items;
+  int64_t slots = 0;
   for (int v = 0; v < kg; ++v)
-    for (int i = 0; i < op->n_inst; ++i) items.push_back({op->inst_len[i], i, v});
+    for (int i = 0; i < op->n_inst; ++i) {
+      items.push_back({op->inst_len[i], i, v});
+      slots += op->inst_len[i] + 1;
+    }
   std::stable_sort(items.begin(), items.end(), [](const PackItem& a, const PackItem& b) { return a.len > b.len; });
-  int ppt = (int)((op->gl_max_n + 1023) / 1024);
-  std::vector<std::vector<PackItem>> packs = pack_items(items, 1024 * (int64_t)ppt);
+  const int ppt_min = (int)((op->gl_max_n + nt - 1) / nt);
   const char* env = getenv("RSV_GL1D_PPT");
   const int forced = env ? atoi(env) : 0;
-  if (forced >= ppt && forced <= 4) {
-    ppt = forced;
-    packs = pack_items(items, 1024 * (int64_t)ppt);
+  const bool force = forced >= ppt_min && forced <= 4;
+  int ppt = 0, wave = 0;
+  int64_t best_waves = 0;
+  std::vector<std::vector<PackItem>> packs;
+  for (int q = force ? forced : ppt_min; q <= (force ? forced : 4); ++q) {
+    const int64_t cap_q = (int64_t)nt * q;
+    int per_sm = 0;
+    cudaError_t e = gl1d_pack_occupancy<R>(q, &per_sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) continue;
+    const int wave_q = op->sm_count * per_sm;
+    std::vector<std::vector<PackItem>> packs_q;
+    int64_t waves = std::max<int64_t>(1, (slots + wave_q * cap_q - 1) / (wave_q * cap_q));
+    while (!pack_lpt(items, cap_q, (int)(waves * wave_q), packs_q)) ++waves;   // ends: one segment per pack fits
+    if (ppt == 0 || waves < best_waves) {
+      ppt = q;
+      wave = wave_q;
+      best_waves = waves;
+      packs.swap(packs_q);
+    }
   }
-  const int cap = 1024 * ppt;
+  if (ppt == 0) return cudaErrorInvalidConfiguration;
+  const int64_t cap = (int64_t)nt * ppt;
   std::vector<int32_t> map(packs.size() * (size_t)cap, -1);
   for (size_t b = 0; b < packs.size(); ++b) {
     int64_t pos = 0;
@@ -476,7 +508,9 @@ static cudaError_t gl1d_build_packs(rsv_operator op, int kg) {
   if (e != cudaSuccess) return e;
   op->pack_kg = kg;
   op->pack_count = (int)packs.size();
+  op->pack_threads = nt;
   op->pack_ppt = ppt;
+  op->pack_wave = wave;
   return cudaSuccess;
 }
 
@@ -490,8 +524,8 @@ static cudaError_t march_tile_direct(rsv_operator op, const MarchTile& t, void* 
       g.steps = t.steps;
       g.n_forced = t.n_forced;
       g.y_first = t.y_first;
-      if (gl1d_pack_wanted(op, t.kg)) {
-        cudaError_t e = gl1d_build_packs(op, t.kg);
+      if (gl1d_pack_wanted<R>(op, t.kg)) {
+        cudaError_t e = gl1d_build_packs<R>(op, t.kg);
         if (e != cudaSuccess) return e;
         return launch_gl1d_pack<R>(g, (const int32_t*)op->pack_map, op->pack_count, op->pack_ppt, state, F, Y,
                                    op->d_flag, op->stream);

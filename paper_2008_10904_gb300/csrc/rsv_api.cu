@@ -275,9 +275,10 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
       path = "cuda-core propagator step";
   }
   const char* contract = (op->prec == RSV_PREC_FP32 && !op->tc_contract_disabled) ? "tcgen05" : "cuda-core";
-  char packs[64] = "";
+  char packs[96] = "";
   if (op->kind == RSV_OP_GL1D && op->pack_kg > 0)
-    snprintf(packs, sizeof(packs), " packed=%d ctas of %d slots", op->pack_count, 1024 * op->pack_ppt);
+    snprintf(packs, sizeof(packs), " packed=%d ctas of %d slots (%dx%d, %d per wave)", op->pack_count,
+             op->pack_threads * op->pack_ppt, op->pack_threads, op->pack_ppt, op->pack_wave);
   char tuned[64] = "";
   if (op->tuned_k > 0) snprintf(tuned, sizeof(tuned), " tuned=%d/%d for k=%d", op->tuned_tile, op->tuned_group, op->tuned_k);
   snprintf(buf, (size_t)buflen,

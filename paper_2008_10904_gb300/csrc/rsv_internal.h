@@ -139,9 +139,10 @@ struct rsv_operator_s {
   // GL1D: tridiagonal coefficients, direct then adjoint: lo, di, up
   void* tri[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int gl_max_n = 0;
-  // packed launch of uneven GL1D batches (built per vector-group size): slot map, CTA count, slots/thread
+  // packed launch of uneven GL1D batches (built per vector-group size): slot map, CTA count, threads
+  // and slots per thread of a CTA, CTAs per wave (SMs x CTAs resident per SM)
   void* pack_map = nullptr;
-  int pack_kg = 0, pack_count = 0, pack_ppt = 0;
+  int pack_kg = 0, pack_count = 0, pack_threads = 0, pack_ppt = 0, pack_wave = 0;
   // Crank-Nicolson (scheme = RSV_SCHEME_CN): host copies of the tridiagonal coefficients (FP64,
   // direct then adjoint: lo, di, up) and, per step h, the cyclic-reduction factors of
   // I - h/2 A on the device: [dir][level][n] for both neighbours, then [dir][n] inverse pivots
@@ -301,8 +302,14 @@ cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y,
 template <typename R>
 cudaError_t launch_gl1d_apply(const Gl1dTile& t, const int32_t* inst_of_point, const void* x, void* y,
                               cudaStream_t st);
-// Batches of uneven instances: CTAs of 1024 threads x ppt slots holding several (instance, vector)
-// segments each (map [n_packs][1024 ppt] of rows, -1 for separators and unused slots).
+// Batches of uneven instances: CTAs of gl1d_pack_threads<R>() threads x ppt slots (ppt 1 to 4) holding
+// several (instance, vector) segments each (map [n_packs][threads * ppt] of rows, -1 for separators and
+// unused slots).  FP32 takes 1024 threads, FP64 512 (twice the registers per slot).
+template <typename R>
+constexpr int gl1d_pack_threads() { return sizeof(R) == 4 ? 1024 : 512; }
+// CTAs of the packed kernel with ppt slots per thread that one SM holds at once.
+template <typename R>
+cudaError_t gl1d_pack_occupancy(int ppt, int* ctas_per_sm);
 template <typename R>
 cudaError_t launch_gl1d_pack(const Gl1dTile& t, const int32_t* map, int n_packs, int ppt, void* u, const void* F,
                              void* Y, int* flag, cudaStream_t st);

@@ -27,7 +27,8 @@ def _dev(x, prec):
 def _uneven_batch(max_len):
     """Instances of the uneven 1-D batch (N log-uniform in [128, 2048], checked decaying): its 25
     shortest and, with max_len = 2048, its 3 longest, 6 test vectors: more (instance, vector) pairs
-    than the GPU has SMs, so the launch packs several per CTA (one or two slots per thread)."""
+    than the GPU has SMs, so the launch packs several per CTA (FP32 CTAs of 1024 threads, FP64 of 512,
+    with the fewest slots per thread that hold the longest instance)."""
     c5 = W.gl_batch_c5().system
     order = sorted(range(len(c5.n)), key=lambda i: c5.n[i])
     keep = order[:25] + (order[-3:] if max_len > 1024 else order[25:28])
@@ -59,7 +60,8 @@ def test_packed_uneven_batch_matches_oracle(rsv, max_len, prec, adjoint):
         y = torch.empty_like(x)
         (rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct)(op, x, w.k, y, **rsv.march_opts_for(w))
         desc = rsv.rsv_describe(op)
-        slots = 1024 if max_len <= 1024 else 2048
+        threads = 1024 if prec == 1 else 512
+        slots = threads * -(-max(w.system.n) // threads)   # the fewest slots per thread holding the longest
         assert f"of {slots} slots" in desc, desc
         err = rel_rows(y.cpu().numpy().astype(np.complex128), ref)
         assert err < (TOL64 if prec == 0 else TOL32), err
@@ -70,7 +72,8 @@ def test_packed_uneven_batch_matches_oracle(rsv, max_len, prec, adjoint):
 @pytest.mark.parametrize("ppt", ["3", "4"])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_packed_more_slots_per_thread(rsv, ppt, prec, monkeypatch):
-    """Three or four slots per thread (the one-wave variants), forced on the same batch."""
+    """Three or four slots per thread forced on the same batch (FP64's 512 threads need four slots for
+    its longest instance, so a forced three is ignored there)."""
     import torch
     monkeypatch.setenv("RSV_GL1D_PPT", ppt)
     w, fh, ref = _uneven_case(2048, False)
@@ -79,7 +82,33 @@ def test_packed_more_slots_per_thread(rsv, ppt, prec, monkeypatch):
         x = _dev(fh, prec)
         y = torch.empty_like(x)
         rsv.rsv_march_direct(op, x, w.k, y, **rsv.march_opts_for(w))
-        assert f"of {1024 * int(ppt)} slots" in rsv.rsv_describe(op)
+        slots = 1024 * int(ppt) if prec == 1 else 2048
+        assert f"of {slots} slots" in rsv.rsv_describe(op)
+        err = rel_rows(y.cpu().numpy().astype(np.complex128), ref)
+        assert err < (TOL64 if prec == 0 else TOL32), err
+    finally:
+        rsv.rsv_destroy_operator(op)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_packed_uneven_batch_trm_tail(rsv, prec, adjoint):
+    """TRM on the packed batch in tiles of 37 steps: one tile straddles the end of the forcing window and
+    the tail's tiles are unforced (no forcing copies, zero forcing reads)."""
+    import torch
+    w = _uneven_batch(1024)
+    fh = W.test_block(w).astype(np.complex64).astype(np.complex128)
+    g = frequencies.make_grid(w.omegas, w.dt)
+    tail = 150
+    assert g.n_t % 37 != 0
+    ref = march.march(operators.gl1d(w.system), g, fh, variant="trm", tail_steps=tail, adjoint=adjoint)
+    op = rsv.create_for_workload(w, prec)
+    try:
+        x = _dev(fh, prec)
+        y = torch.empty_like(x)
+        (rsv.rsv_march_adjoint if adjoint else rsv.rsv_march_direct)(op, x, w.k, y, variant="trm",
+                                                                      tail_steps=tail, tile_steps=37)
+        assert "packed=" in rsv.rsv_describe(op)
         err = rel_rows(y.cpu().numpy().astype(np.complex128), ref)
         assert err < (TOL64 if prec == 0 else TOL32), err
     finally:
