@@ -756,6 +756,11 @@ __global__ void __launch_bounds__(NT, MINB) adv3d_pair_kernel(StGeom g, Pair3D P
   const float c1 = PAIR_B ? h : 0.5f * h;       // x_mid = u + c1 (A x + f_a)
   const float c2 = PAIR_B ? h / 6.f : 0.5f * h;  // pair A: x3 = u + h/2 k2; pair B: u' = ... + h/6 k4
   const int tid = threadIdx.x;
+  // Launched as a programmatic dependent of the previous pair kernel, the CTA may be resident before
+  // that kernel ends: it waits for it here, before any memory access (a no-op after an ordinary
+  // launch), and then lets the next kernel launch, whose CTAs wait in the same place.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // The forward first stage evaluates all its slots as one straight-line block (masked afterwards);
   // the transposed one (five base-flow values per cell) keeps a branch per slot, which holds it
   // under the register limit without spills (the flat form spilled and measured 2.3% slower).
@@ -1117,6 +1122,16 @@ int pair3d_zchunks(int per_chunk, int nz, int resident) {
   return best;
 }
 
+// Programmatic dependent launch of the pair kernels: on (default) or off (RSV_PAIR3D_PDL=0), read once
+// per process.
+bool pair3d_pdl() {
+  static bool v = [] {
+    const char* e = getenv("RSV_PAIR3D_PDL");
+    return !(e != nullptr && e[0] == '0');
+  }();
+  return v;
+}
+
 template <bool ADJ, bool PAIR_B, int MINB, int TY, int NT>
 cudaError_t launch_pair3d_minb(rsv_operator op, const StGeom& g, const Pair3D& P0) {
   constexpr size_t smem = pair3d_smem<TY>();
@@ -1146,8 +1161,19 @@ cudaError_t launch_pair3d_minb(rsv_operator op, const StGeom& g, const Pair3D& P
   Pair3D P = P0;
   P.zchunks = pair3d_zchunks((int)(ntx * nty) * g.kg, g.nz, resident);
   const unsigned blocks = ntx * nty * (unsigned)P.zchunks * (unsigned)g.kg;
-  adv3d_pair_kernel<ADJ, PAIR_B, MINB, TY, NT><<<blocks, NT, smem, op->stream>>>(g, P);
-  return cudaGetLastError();
+  // programmatic dependent launch: the kernel may start as the previous one drains (the kernel
+  // orders its reads and writes around griddepcontrol.wait)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = op->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pair3d_pdl() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, adv3d_pair_kernel<ADJ, PAIR_B, MINB, TY, NT>, g, P);
 }
 
 // Tile height of the pair kernels: 8 (default) or 16 (RSV_PAIR3D_TY=16), read once per process.
