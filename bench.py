@@ -216,7 +216,7 @@ def load_peaks():
 #   2-D march    adr2d_pair_c3.txt: the two stage-pair kernels of one step at 16 vectors,
 #                342.9 MB per step, scaled by 255 steps (traffic per step is constant)
 #   3-D march    adv3d_pair_c4.txt: the two stage-pair kernels of one step at 2 vectors,
-#                1347.2 MB per step, scaled by 255 steps
+#                1347.6 MB per step, scaled by 255 steps
 TRAFFIC = {
     ("dense_hermite_gl_n1024_k32_w256_trm", "march", 256, 32768):
         {"bytes": 108.98e6, "src": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"},
@@ -225,7 +225,7 @@ TRAFFIC = {
     ("adr2d_1024x512_k16_w128_ssrm", "march", 255, 8388608):
         {"bytes": 255 * 342.9e6, "src": "ncu dram bytes of the two stage-pair kernels of one step x 255 steps"},
     ("adv3d_256x128x128x3_k8_w64_ssrm", "march", 255, 25165824):
-        {"bytes": 255 * 1347.2e6, "src": "ncu dram bytes of the two stage-pair kernels of one step x 255 steps"},
+        {"bytes": 255 * 1347.6e6, "src": "ncu dram bytes of the two stage-pair kernels of one step x 255 steps"},
 }
 
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
