@@ -28,6 +28,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -353,6 +354,25 @@ def _oracle_sample(name, steps, k_sample, one_row, threads, warmup=0, repeats=1)
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (x86: /proc/cpuinfo; Arm: lscpu), else the machine type."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(name: str, target_seconds: float = 15.0, warmup: int = 0, repeats: int = 1):
     """The oracle, as it stands, on the host's cores (BLAS threads), on a bounded sample of one march.
 
@@ -367,10 +387,8 @@ def cpu_baseline(name: str, target_seconds: float = 15.0, warmup: int = 0, repea
     one_row = w.n * w.n_omega > (1 << 28)
     probe = 1 if huge else (10 if type(w.system).__name__ in ("Dense", "ADV3D") else 100)
     try:
-        steps = probe
-        if not huge:
-            d = _oracle_sample(name, probe, k_sample, one_row, cores)
-            steps = max(probe, min(d["total_steps"], int(target_seconds / (d["seconds"] / d["steps"]))))
+        d = _oracle_sample(name, probe, k_sample, one_row, cores)
+        steps = max(probe, min(d["total_steps"], int(target_seconds / (d["seconds"] / d["steps"]))))
         d = _oracle_sample(name, steps, k_sample, one_row, cores, warmup, repeats)
     except (RuntimeError, subprocess.TimeoutExpired) as e:
         return {"value": None, "unit": "actions/s", "cores": cores, "kind": "oracle", "error": str(e)[-400:]}
@@ -384,7 +402,7 @@ def cpu_baseline(name: str, target_seconds: float = 15.0, warmup: int = 0, repea
     if one_row:
         sample += "; one seeded test-vector row serves every frequency (same work, fewer random draws)"
     return {"value": actions_per_march(w) / march_s, "unit": "actions/s", "cores": cores, "kind": "oracle",
-            "sample": sample, "seconds": d["seconds"], "samples": samples}
+            "cpu_model": cpu_model(), "sample": sample, "seconds": d["seconds"], "samples": samples}
 
 
 # ---------------------------------------------------------------------------
