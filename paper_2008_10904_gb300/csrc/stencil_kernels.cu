@@ -602,16 +602,12 @@ cudaError_t launch_adr2d_step(rsv_operator op, const StGeom& g, const R* uin, R*
 // against about 20 for the four single-stage kernels; halo cells come from L2.
 // Cells outside the grid hold zero (homogeneous Dirichlet), in both rings.
 // ---------------------------------------------------------------------------
-constexpr int k3TX = 64, k3TY = 8, k3ZC = 16;
-constexpr int k3UW = k3TX + 8, k3UH = k3TY + 4;     // ring of the pair's stencil input: x from X0 - 4
-                                                    // (16-byte aligned rows), halo 2 used, y halo 2
-constexpr int k3XW = k3TX + 2, k3XH = k3TY + 2;     // ring of the intermediate stage (halo 1)
-constexpr int k3UP = k3UW * k3UH, k3XP = k3XW * k3XH;
-constexpr int k3Threads = 256;
-constexpr int k3S1 = (k3XP + k3Threads - 1) / k3Threads;   // first-stage cells per thread (3)
-constexpr int k3S2 = k3TX * k3TY / k3Threads;              // second-stage cells per thread (2)
-constexpr int k3Row4 = k3UW / 4;                           // 16-byte chunks per ring row (18)
-constexpr size_t k3Smem = sizeof(float) * (4 * 3 * (size_t)k3UP + 3 * 3 * (size_t)k3XP);
+// Tile width and the ring row widths; each kernel variant derives its heights from its tile height.
+constexpr int k3TX = 64, k3ZC = 16;
+constexpr int k3UW = k3TX + 8;     // ring of the pair's stencil input: x from X0 - 4 (16-byte aligned
+                                   // rows), halo 2 used; y halo 2
+constexpr int k3XW = k3TX + 2;     // ring of the intermediate stage (halo 1)
+constexpr int k3Row4 = k3UW / 4;   // 16-byte chunks per ring row (18)
 
 struct Pair3D {
   const float* in;     // stencil input of the first stage: u (pair A) or x3 (pair B)
@@ -716,7 +712,7 @@ constexpr size_t pair3d_smem() {
 // Requires nx % 4 == 0 (16-byte rows of the input ring) and n < 2^31 (32-bit offsets in a vector).
 template <bool ADJ, bool PAIR_B, int MINB, int TY, int NT>
 __global__ void __launch_bounds__(NT, MINB) adv3d_pair_kernel(StGeom g, Pair3D P) {
-  // this variant's tile geometry (the namespace-level constants describe the 64 x 8 variant)
+  // this variant's tile geometry (heights and slots follow from its tile height TY and threads NT)
   constexpr int k3TY = TY, k3Threads = NT;
   constexpr int k3UH = k3TY + 4, k3XH = k3TY + 2;
   constexpr int k3UP = k3UW * k3UH, k3XP = k3XW * k3XH;
@@ -942,7 +938,6 @@ __global__ void __launch_bounds__(NT, MINB) adv3d_pair_kernel(StGeom g, Pair3D P
 constexpr int k2TX = 64, k2TY = 32, k2Threads = 256;
 constexpr int k2UW = k2TX + 8, k2UH = k2TY + 4;     // input tile: x from X0 - 4, y halo 2
 constexpr int k2XW = k2TX + 2, k2XH = k2TY + 2;     // first-stage tile: halo 1
-constexpr int k2Row4 = k2UW / 4;
 
 // Sponge rate at cell (gi, gj) with precomputed 1 / sponge_cells (the same values as sponge()).
 __device__ __forceinline__ float sponge_fast(int gi, int gj, const StGeom& g, float inv_s) {
