@@ -115,6 +115,53 @@ def test_packed_uneven_batch_trm_tail(rsv, prec, adjoint):
         rsv.rsv_destroy_operator(op)
 
 
+def _fp32_tolerance(a, h):
+    """FP32 march tolerance of one instance: rounding (6e-8 per operation, about eight roundings per
+    step reaching the state) accumulates like a random walk over the slowest mode's decay time,
+    1 / (|spectral abscissa| h) steps; twice that estimate, and no less than the short cases' 2e-5."""
+    import scipy.sparse as sp
+    dense = a.toarray() if sp.issparse(a) else np.asarray(a)
+    decay_steps = 1.0 / (abs(np.linalg.eigvals(dense).real.max()) * h)
+    return max(TOL32, 2 * 6e-8 * 8 * np.sqrt(decay_steps))
+
+
+@pytest.mark.slow
+def test_packed_full_batch_in_bench_launch_sampled(rsv):
+    """The full 64-instance batch with its 8 test vectors in one group, in the bench's launch
+    configuration (one wave of 152 CTAs x 3072 slots, three per thread), on the first 4 frequencies of
+    its grid over one window (the window and the step are those of the full grid; the packing depends
+    only on the instances and the vector group).  The shortest, the median and the longest instance,
+    vectors 0 and 7, against the oracle marching each instance alone (the batch's operator is block
+    diagonal), per frequency row, FP32."""
+    import torch
+    c5 = W.gl_batch_c5()
+    w = W.Workload("gl_batch_sample", c5.system, c5.omegas[:4], c5.dt, c5.k, "ssrm", n_transient_windows=0,
+                   seed=W.SEED_BASE + 75)
+    fh = W.test_block(w).astype(np.complex64).astype(np.complex128)
+    op = rsv.create_for_workload(w, 1)
+    try:
+        x = _dev(fh, 1)
+        y = torch.empty_like(x)
+        rsv.rsv_march_direct(op, x, w.k, y, **rsv.march_opts_for(w))
+        desc = rsv.rsv_describe(op)
+        assert "packed=152 ctas of 3072 slots (1024x3" in desc and "group=8" in desc, desc
+        got = y.cpu().numpy().astype(np.complex128)
+    finally:
+        rsv.rsv_destroy_operator(op)
+    g = frequencies.make_grid(w.omegas, w.dt)
+    n = list(w.system.n)
+    off = np.concatenate([[0], np.cumsum(n)])
+    order = sorted(range(len(n)), key=lambda i: n[i])
+    vecs = [0, w.k - 1]
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        a = operators.gl1d(W.GL1D(n=(n[i],), mu0=(w.system.mu0[i],)))
+        seg = slice(off[i], off[i + 1])
+        ref = march.march(a, g, fh[:, vecs, seg], variant="ssrm", n_trans=0)
+        err = rel_rows(got[:, vecs, seg], ref)
+        tol = _fp32_tolerance(a, g.h)
+        assert err < tol, (i, n[i], err, tol)
+
+
 def _adr(k=3):
     sysm = W.ADR2D(nx=40, ny=24, lx=40.0, ly=10.0, sponge_cells=4)
     dx = sysm.lx / (sysm.nx + 1)
