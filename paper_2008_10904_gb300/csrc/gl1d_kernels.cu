@@ -14,6 +14,8 @@
 //   k3 = A (u + h/2 k2) + f(t_n + h/2)
 //   k4 = A (u + h k3)   + f(t_n + h)
 //   u <- u + h/6 (k1 + 2 k2 + 2 k3 + k4)
+#include <cooperative_groups.h>
+
 #include "rsv_internal.h"
 
 namespace rsv {
@@ -164,6 +166,122 @@ __global__ void __launch_bounds__(MAXT) gl1d_tile_kernel(Gl1dTile t, cpx<R>* __r
     if (norms != nullptr) norms[(int64_t)v * t.n_inst + inst] = tot;
     if (!(tot < 1e300)) atomicExch(flag, 1);  // NaN or overflow
   }
+}
+
+// RK4 tile kernel for a few long FP64 marches (fewer (instance, vector) pairs than SMs): one
+// thread-block cluster of CS CTAs per pair, each CTA owning a contiguous chunk of ceil(len / CS) of the
+// instance's points, one per thread, so that the FP64 arithmetic of one march (the limit of the
+// one-CTA kernel: FP64 runs at a small fraction of the FP32 rate) is spread over CS SMs.  The stage
+// input is exchanged through shared memory as in gl1d_tile_kernel; a chunk's end points read their
+// outer neighbours from the adjacent CTAs' shared memory (distributed shared memory) after a cluster
+// barrier, which takes the place of the CTA barrier.  Every CTA of a cluster, including one that owns
+// no point, runs the same sequence of cluster barriers; the last one keeps each CTA resident until its
+// neighbours' reads of its shared memory are done.
+template <typename R, int CS>
+__global__ void gl1d_cluster_kernel(Gl1dTile t, cpx<R>* __restrict__ u, const cpx<R>* __restrict__ F,
+                                    cpx<R>* __restrict__ Y, double* __restrict__ norms, int* __restrict__ flag) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ double red[32];
+  __shared__ double part;
+  const int rank = (int)cluster.block_rank();
+  const int inst = blockIdx.x / CS;
+  const int v = blockIdx.y;
+  const int64_t off = t.inst_off[inst];
+  const int len = (int)(t.inst_off[inst + 1] - off);
+  const int ch = (len + CS - 1) / CS;            // points per CTA of this instance
+  const int p0 = rank * ch;                       // first point of this CTA
+  const int cnt = max(0, min(ch, len - p0));      // points it owns (the last CTAs may own fewer or none)
+  const int ld = (int)blockDim.x + 2;
+  cpx<R>* sx = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][blockDim + 2]: point j of the chunk at slot 1 + j
+  const cpx<R>* lo = reinterpret_cast<const cpx<R>*>(t.lo);
+  const cpx<R>* di = reinterpret_cast<const cpx<R>*>(t.di);
+  const cpx<R>* up = reinterpret_cast<const cpx<R>*>(t.up);
+  const cpx<R> zero = mk<R>(0, 0);
+  const int i = threadIdx.x;
+  const bool ok = i < cnt;
+  // the neighbours beyond the chunk's ends: the left CTA's last point and the right CTA's first
+  // (both CTAs own full chunks when they exist); zero at the instance's Dirichlet ends
+  const bool has_left = cnt > 0 && rank > 0;
+  const bool has_right = cnt > 0 && p0 + ch < len;
+  const cpx<R>* left_sx = has_left ? cluster.map_shared_rank(sx, rank - 1) : nullptr;
+  const cpx<R>* right_sx = has_right ? cluster.map_shared_rank(sx, rank + 1) : nullptr;
+  const int64_t rows = (int64_t)t.kg * t.n;
+  const int64_t r = (int64_t)v * t.n + off + p0 + i;    // this thread's row (when ok)
+  cpx<R> cl = zero, cd = zero, cu = zero, us = zero;
+  if (ok) {
+    cl = lo[off + p0 + i];
+    cd = di[off + p0 + i];
+    cu = up[off + p0 + i];
+    us = u[r];
+  }
+  const R h = R(t.h);
+  const R h2 = R(0.5) * h;
+  const R h6 = h / R(6);
+  int buf = 0;
+  auto stage = [&](const cpx<R>& x, const cpx<R>& f) -> cpx<R> {
+    cpx<R>* s = sx + buf * ld;
+    if (ok) s[1 + i] = x;
+    cluster.sync();
+    cpx<R> a = f;
+    if (ok) {
+      const cpx<R> xl = i > 0 ? s[i] : (has_left ? left_sx[buf * ld + ch] : zero);
+      const cpx<R> xr = i + 1 < cnt ? s[i + 2] : (has_right ? right_sx[buf * ld + 1] : zero);
+      cfma(a, cl, xl);
+      cfma(a, cd, x);
+      cfma(a, cu, xr);
+    }
+    buf ^= 1;
+    return a;
+  };
+  auto forced = [&](int s) { return F != nullptr && t.n0 + s < t.n_forced; };
+  cpx<R> f0 = zero, fh = zero, f1 = zero, nfh = zero, nf1 = zero;
+  if (ok && forced(0)) {
+    f0 = F[r];
+    fh = F[rows + r];
+    f1 = F[2 * rows + r];
+  }
+  for (int s = 0; s < t.steps; ++s) {
+    if (ok && s + 1 < t.steps && forced(s + 1)) {   // next step's forcing, in flight during this step
+      nfh = F[(int64_t)(2 * s + 3) * rows + r];
+      nf1 = F[(int64_t)(2 * s + 4) * rows + r];
+    }
+    if (!forced(s)) f0 = fh = f1 = zero;
+    if (ok && Y != nullptr && s >= t.y_first) Y[(int64_t)s * rows + r] = us;
+    cpx<R> k = stage(us, f0);
+    cpx<R> acc = k;
+    k = stage(us + h2 * k, fh);
+    acc = acc + R(2) * k;
+    k = stage(us + h2 * k, fh);
+    acc = acc + R(2) * k;
+    k = stage(us + h * k, f1);
+    us = us + h6 * (acc + k);
+    f0 = f1;
+    fh = nfh;
+    f1 = nf1;
+  }
+  double nrm = 0.0;
+  if (ok) {
+    u[r] = us;
+    nrm = (double)us.re * (double)us.re + (double)us.im * (double)us.im;
+  }
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if ((i & 31) == 0) red[i >> 5] = nrm;
+  __syncthreads();
+  if (i == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    part = tot;
+  }
+  cluster.sync();
+  if (rank == 0 && i == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < CS; ++q) tot += *cluster.map_shared_rank(&part, q);
+    if (norms != nullptr) norms[(int64_t)v * t.n_inst + inst] = tot;
+    if (!(tot < 1e300)) atomicExch(flag, 1);  // NaN or overflow
+  }
+  cluster.sync();
 }
 
 // Crank-Nicolson tile kernel (the time scheme of the paper's Sec. 3 case):
@@ -475,14 +593,61 @@ cudaError_t launch_ppt(const Gl1dTile& t, int threads, void* u, const void* F, v
   return cudaGetLastError();
 }
 
+// One cluster of CS CTAs per (instance, vector), one point per thread.
+template <typename R, int CS>
+cudaError_t launch_cluster(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms, int* flag,
+                           cudaStream_t st) {
+  const int chunk = (t.max_n + CS - 1) / CS;
+  const int threads = (chunk + 31) / 32 * 32;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(CS * t.n_inst), (unsigned)t.kg);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = sizeof(cpx<R>) * 2 * (size_t)(threads + 2);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gl1d_cluster_kernel<R, CS>, t, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y, norms,
+                            flag);
+}
+
 }  // namespace
 
+// Cluster size for the FP64 RK4 march (0: one CTA per pair): the largest of 8, 4, 2 for which every
+// (instance, vector) pair's cluster fits in one wave and every CTA of the longest instance owns 32 to
+// 256 points.  RSV_GL1D_CLUSTER=0 keeps one CTA per pair.
+int gl1d_cluster_size(const Gl1dTile& t) {
+  static const bool env = [] {
+    const char* e = getenv("RSV_GL1D_CLUSTER");
+    return !(e != nullptr && e[0] == '0');
+  }();
+  if (!env || t.cr_levels > 0) return 0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  for (int cs = 8; cs >= 2; cs /= 2)
+    if (t.max_n >= 32 * cs && (t.max_n + cs - 1) / cs <= 256 && (int64_t)t.n_inst * t.kg * cs <= sms) return cs;
+  return 0;
+}
+
 // One CTA per (instance, vector); PPT points per thread, interleaved (point
-// i = thread + m * blockDim) so that every load and store is coalesced.
+// i = thread + m * blockDim) so that every load and store is coalesced.  FP64
+// marches of few pairs take a cluster of CTAs per pair instead.
 template <typename R>
 cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms, int* flag,
                              cudaStream_t st) {
   if (t.max_n > 4096) return cudaErrorInvalidValue;
+  if constexpr (sizeof(R) == 8) {   // FP64: spread each march over a cluster of SMs when there are few
+    const int cs = gl1d_cluster_size(t);
+    if (cs == 8) return launch_cluster<R, 8>(t, u, F, Y, norms, flag, st);
+    if (cs == 4) return launch_cluster<R, 4>(t, u, F, Y, norms, flag, st);
+    if (cs == 2) return launch_cluster<R, 2>(t, u, F, Y, norms, flag, st);
+  }
   const int ppt = t.max_n <= 1024 ? 1 : (t.max_n <= 2048 ? 2 : 4);
   const int threads = (((t.max_n + ppt - 1) / ppt + 31) / 32) * 32;
   if (ppt == 1) return launch_ppt<R, 1, 1024>(t, threads, u, F, Y, norms, flag, st);

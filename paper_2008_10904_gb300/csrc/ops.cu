@@ -530,6 +530,7 @@ static cudaError_t march_tile_direct(rsv_operator op, const MarchTile& t, void* 
         return launch_gl1d_pack<R>(g, (const int32_t*)op->pack_map, op->pack_count, op->pack_ppt, state, F, Y,
                                    op->d_flag, op->stream);
       }
+      if (sizeof(R) == 8) op->gl_cluster = gl1d_cluster_size(g);
       return launch_gl1d_tile<R>(g, state, F, Y, norms, op->d_flag, op->stream);
     }
     case RSV_OP_DENSE: {

@@ -279,6 +279,8 @@ extern "C" rsv_status rsv_describe(rsv_operator op, char* buf, int32_t buflen) {
   if (op->kind == RSV_OP_GL1D && op->pack_kg > 0)
     snprintf(packs, sizeof(packs), " packed=%d ctas of %d slots (%dx%d, %d per wave)", op->pack_count,
              op->pack_threads * op->pack_ppt, op->pack_threads, op->pack_ppt, op->pack_wave);
+  else if (op->kind == RSV_OP_GL1D && op->gl_cluster > 0)
+    snprintf(packs, sizeof(packs), " cluster=%d ctas per march", op->gl_cluster);
   char tuned[64] = "";
   if (op->tuned_k > 0) snprintf(tuned, sizeof(tuned), " tuned=%d/%d for k=%d", op->tuned_tile, op->tuned_group, op->tuned_k);
   snprintf(buf, (size_t)buflen,

@@ -143,6 +143,8 @@ struct rsv_operator_s {
   // and slots per thread of a CTA, CTAs per wave (SMs x CTAs resident per SM)
   void* pack_map = nullptr;
   int pack_kg = 0, pack_count = 0, pack_threads = 0, pack_ppt = 0, pack_wave = 0;
+  // FP64 RK4 GL1D marches: CTAs per (instance, vector) cluster of the last tile (0: one CTA)
+  int gl_cluster = 0;
   // Crank-Nicolson (scheme = RSV_SCHEME_CN): host copies of the tridiagonal coefficients (FP64,
   // direct then adjoint: lo, di, up) and, per step h, the cyclic-reduction factors of
   // I - h/2 A on the device: [dir][level][n] for both neighbours, then [dir][n] inverse pivots
@@ -299,6 +301,8 @@ struct Gl1dTile {
 template <typename R>
 cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms,
                              int* flag, cudaStream_t st);
+// Cluster size the FP64 RK4 tile launch takes for this tile (0: one CTA per (instance, vector)).
+int gl1d_cluster_size(const Gl1dTile& t);
 template <typename R>
 cudaError_t launch_gl1d_apply(const Gl1dTile& t, const int32_t* inst_of_point, const void* x, void* y,
                               cudaStream_t st);
