@@ -169,14 +169,20 @@ __global__ void __launch_bounds__(MAXT) gl1d_tile_kernel(Gl1dTile t, cpx<R>* __r
 }
 
 // RK4 tile kernel for a few long FP64 marches (fewer (instance, vector) pairs than SMs): one
-// thread-block cluster of CS CTAs per pair, each CTA owning a contiguous chunk of ceil(len / CS) of the
-// instance's points, one per thread, so that the FP64 arithmetic of one march (the limit of the
-// one-CTA kernel: FP64 runs at a small fraction of the FP32 rate) is spread over CS SMs.  The stage
-// input is exchanged through shared memory as in gl1d_tile_kernel; a chunk's end points read their
-// outer neighbours from the adjacent CTAs' shared memory (distributed shared memory) after a cluster
-// barrier, which takes the place of the CTA barrier.  Every CTA of a cluster, including one that owns
-// no point, runs the same sequence of cluster barriers; the last one keeps each CTA resident until its
-// neighbours' reads of its shared memory are done.
+// thread-block cluster of CS CTAs per pair, each CTA owning a contiguous chunk of ch = ceil(len / CS) of
+// the instance's points, so that the FP64 arithmetic of one march (the limit of the one-CTA kernel:
+// FP64 runs at a small fraction of the FP32 rate) is spread over CS SMs.  A cluster barrier costs far
+// more than a CTA barrier, so there is one per step, not one per stage: at the start of a step every
+// CTA publishes its chunk's state in shared memory, and after the cluster barrier reads the kHalo = 4
+// points beyond each end of its chunk from the CTAs that own them (distributed shared memory).  It then
+// takes the four RK4 stages on the widened range [-kHalo, ch + kHalo) with CTA barriers only: a stage
+// is exact wherever its input is exact at the point and both neighbours, so the exact range shrinks by
+// one point per side and stage and after four stages still covers the chunk.  Points outside the
+// instance have zero coefficients, forcing and state, and stay zero (the Dirichlet ends).  Every CTA of a
+// cluster, including one that owns no point, runs the same sequence of cluster barriers; the last one
+// keeps each CTA resident until the other CTAs' reads of its shared memory are done.
+constexpr int kHalo = 4;
+
 template <typename R, int CS>
 __global__ void gl1d_cluster_kernel(Gl1dTile t, cpx<R>* __restrict__ u, const cpx<R>* __restrict__ F,
                                     cpx<R>* __restrict__ Y, double* __restrict__ norms, int* __restrict__ flag) {
@@ -193,62 +199,70 @@ __global__ void gl1d_cluster_kernel(Gl1dTile t, cpx<R>* __restrict__ u, const cp
   const int ch = (len + CS - 1) / CS;            // points per CTA of this instance
   const int p0 = rank * ch;                       // first point of this CTA
   const int cnt = max(0, min(ch, len - p0));      // points it owns (the last CTAs may own fewer or none)
-  const int ld = (int)blockDim.x + 2;
-  cpx<R>* sx = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][blockDim + 2]: point j of the chunk at slot 1 + j
+  const int nt = (int)blockDim.x;                 // >= ch_max + 2 kHalo
+  const int pub = nt - 2 * kHalo;                 // >= the longest chunk
+  cpx<R>* sx = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][nt + 2]: position e at slot 1 + e
+  cpx<R>* ush = sx + 2 * (nt + 2);                  // [2][pub]: the chunk's state, published per step
   const cpx<R>* lo = reinterpret_cast<const cpx<R>*>(t.lo);
   const cpx<R>* di = reinterpret_cast<const cpx<R>*>(t.di);
   const cpx<R>* up = reinterpret_cast<const cpx<R>*>(t.up);
   const cpx<R> zero = mk<R>(0, 0);
-  const int i = threadIdx.x;
-  const bool ok = i < cnt;
-  // the neighbours beyond the chunk's ends: the left CTA's last point and the right CTA's first
-  // (both CTAs own full chunks when they exist); zero at the instance's Dirichlet ends
-  const bool has_left = cnt > 0 && rank > 0;
-  const bool has_right = cnt > 0 && p0 + ch < len;
-  const cpx<R>* left_sx = has_left ? cluster.map_shared_rank(sx, rank - 1) : nullptr;
-  const cpx<R>* right_sx = has_right ? cluster.map_shared_rank(sx, rank + 1) : nullptr;
+  const int e = threadIdx.x;                      // position on the widened range
+  const int j = e - kHalo;                        // point index relative to the chunk
+  const int q = p0 + j;                           // point index in the instance
+  const bool inside = j < ch + kHalo && q >= 0 && q < len;
+  const bool owned = j >= 0 && j < cnt;
   const int64_t rows = (int64_t)t.kg * t.n;
-  const int64_t r = (int64_t)v * t.n + off + p0 + i;    // this thread's row (when ok)
+  const int64_t r = (int64_t)v * t.n + off + q;   // this position's row (when inside)
+  // owner of a halo point and its slot in the owner's published chunk
+  const cpx<R>* halo_src = nullptr;
+  if (inside && !owned) halo_src = cluster.map_shared_rank(ush, q / ch) + q % ch;
   cpx<R> cl = zero, cd = zero, cu = zero, us = zero;
-  if (ok) {
-    cl = lo[off + p0 + i];
-    cd = di[off + p0 + i];
-    cu = up[off + p0 + i];
-    us = u[r];
+  if (inside) {
+    cl = lo[off + q];
+    cd = di[off + q];
+    cu = up[off + q];
   }
+  if (owned) us = u[r];
+  for (int i = threadIdx.x; i < 2 * (nt + 2); i += nt) sx[i] = zero;   // the range's outer slots stay zero
+  __syncthreads();
   const R h = R(t.h);
   const R h2 = R(0.5) * h;
   const R h6 = h / R(6);
   int buf = 0;
+  // y = A x + f on the widened range (CTA barrier; the range's ends read zero)
   auto stage = [&](const cpx<R>& x, const cpx<R>& f) -> cpx<R> {
-    cpx<R>* s = sx + buf * ld;
-    if (ok) s[1 + i] = x;
-    cluster.sync();
+    cpx<R>* s = sx + buf * (nt + 2);
+    s[1 + e] = x;
+    __syncthreads();
     cpx<R> a = f;
-    if (ok) {
-      const cpx<R> xl = i > 0 ? s[i] : (has_left ? left_sx[buf * ld + ch] : zero);
-      const cpx<R> xr = i + 1 < cnt ? s[i + 2] : (has_right ? right_sx[buf * ld + 1] : zero);
-      cfma(a, cl, xl);
-      cfma(a, cd, x);
-      cfma(a, cu, xr);
-    }
+    cfma(a, cl, s[e]);
+    cfma(a, cd, x);
+    cfma(a, cu, s[e + 2]);
     buf ^= 1;
     return a;
   };
   auto forced = [&](int s) { return F != nullptr && t.n0 + s < t.n_forced; };
   cpx<R> f0 = zero, fh = zero, f1 = zero, nfh = zero, nf1 = zero;
-  if (ok && forced(0)) {
+  if (inside && forced(0)) {
     f0 = F[r];
     fh = F[rows + r];
     f1 = F[2 * rows + r];
   }
   for (int s = 0; s < t.steps; ++s) {
-    if (ok && s + 1 < t.steps && forced(s + 1)) {   // next step's forcing, in flight during this step
+    if (inside && s + 1 < t.steps && forced(s + 1)) {   // next step's forcing, in flight during this step
       nfh = F[(int64_t)(2 * s + 3) * rows + r];
       nf1 = F[(int64_t)(2 * s + 4) * rows + r];
     }
     if (!forced(s)) f0 = fh = f1 = zero;
-    if (ok && Y != nullptr && s >= t.y_first) Y[(int64_t)s * rows + r] = us;
+    // publish the chunk's state, then take the halo's from its owners
+    cpx<R>* pubs = ush + (s & 1) * pub;
+    if (owned) {
+      pubs[j] = us;
+      if (Y != nullptr && s >= t.y_first) Y[(int64_t)s * rows + r] = us;
+    }
+    cluster.sync();
+    if (halo_src != nullptr) us = halo_src[(s & 1) * pub];
     cpx<R> k = stage(us, f0);
     cpx<R> acc = k;
     k = stage(us + h2 * k, fh);
@@ -256,28 +270,28 @@ __global__ void gl1d_cluster_kernel(Gl1dTile t, cpx<R>* __restrict__ u, const cp
     k = stage(us + h2 * k, fh);
     acc = acc + R(2) * k;
     k = stage(us + h * k, f1);
-    us = us + h6 * (acc + k);
+    us = owned ? us + h6 * (acc + k) : zero;
     f0 = f1;
     fh = nfh;
     f1 = nf1;
   }
   double nrm = 0.0;
-  if (ok) {
+  if (owned) {
     u[r] = us;
     nrm = (double)us.re * (double)us.re + (double)us.im * (double)us.im;
   }
   for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-  if ((i & 31) == 0) red[i >> 5] = nrm;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
   __syncthreads();
-  if (i == 0) {
+  if (threadIdx.x == 0) {
     double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    for (int w = 0; w < nt / 32; ++w) tot += red[w];
     part = tot;
   }
   cluster.sync();
-  if (rank == 0 && i == 0) {
+  if (rank == 0 && threadIdx.x == 0) {
     double tot = 0.0;
-    for (int q = 0; q < CS; ++q) tot += *cluster.map_shared_rank(&part, q);
+    for (int c = 0; c < CS; ++c) tot += *cluster.map_shared_rank(&part, c);
     if (norms != nullptr) norms[(int64_t)v * t.n_inst + inst] = tot;
     if (!(tot < 1e300)) atomicExch(flag, 1);  // NaN or overflow
   }
@@ -598,11 +612,11 @@ template <typename R, int CS>
 cudaError_t launch_cluster(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms, int* flag,
                            cudaStream_t st) {
   const int chunk = (t.max_n + CS - 1) / CS;
-  const int threads = (chunk + 31) / 32 * 32;
+  const int threads = (chunk + 2 * kHalo + 31) / 32 * 32;   // the widened range of the longest chunk
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(CS * t.n_inst), (unsigned)t.kg);
   cfg.blockDim = dim3((unsigned)threads);
-  cfg.dynamicSmemBytes = sizeof(cpx<R>) * 2 * (size_t)(threads + 2);
+  cfg.dynamicSmemBytes = sizeof(cpx<R>) * (2 * (size_t)(threads + 2) + 2 * (size_t)(threads - 2 * kHalo));
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
