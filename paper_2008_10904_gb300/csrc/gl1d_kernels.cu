@@ -16,6 +16,8 @@
 //   u <- u + h/6 (k1 + 2 k2 + 2 k3 + k4)
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "rsv_internal.h"
 
 namespace rsv {
@@ -172,21 +174,20 @@ __global__ void __launch_bounds__(MAXT) gl1d_tile_kernel(Gl1dTile t, cpx<R>* __r
 // thread-block cluster of CS CTAs per pair, each CTA owning a contiguous chunk of ch = ceil(len / CS) of
 // the instance's points, so that the FP64 arithmetic of one march (the limit of the one-CTA kernel:
 // FP64 runs at a small fraction of the FP32 rate) is spread over CS SMs.  A cluster barrier costs far
-// more than a CTA barrier, so there is one per step, not one per stage: at the start of a step every
-// CTA publishes its chunk's state in shared memory, and after the cluster barrier reads the kHalo = 4
-// points beyond each end of its chunk from the CTAs that own them (distributed shared memory).  It then
-// takes the four RK4 stages on the widened range [-kHalo, ch + kHalo) with CTA barriers only: a stage
-// is exact wherever its input is exact at the point and both neighbours, so the exact range shrinks by
-// one point per side and stage and after four stages still covers the chunk.  Points outside the
+// more than a CTA barrier, so there is one per M steps, not one per stage: every M steps each CTA
+// publishes its chunk's state in shared memory, and after the cluster barrier reads the H = 4 M points
+// beyond each end of its chunk from the CTAs that own them (distributed shared memory).  It then takes
+// M steps of four RK4 stages on the widened range [-H, ch + H) with CTA barriers only: a stage is
+// exact wherever its input is exact at the point and both neighbours, so the exact range shrinks by
+// one point per side and stage and after 4 M stages still covers the chunk.  Points outside the
 // instance have zero coefficients, forcing and state, and stay zero (the Dirichlet ends).  Every CTA of a
 // cluster, including one that owns no point, runs the same sequence of cluster barriers; the last one
 // keeps each CTA resident until the other CTAs' reads of its shared memory are done.
-constexpr int kHalo = 4;
-
-template <typename R, int CS>
+template <typename R, int CS, int M>
 __global__ void gl1d_cluster_kernel(Gl1dTile t, cpx<R>* __restrict__ u, const cpx<R>* __restrict__ F,
                                     cpx<R>* __restrict__ Y, double* __restrict__ norms, int* __restrict__ flag) {
   namespace cg = cooperative_groups;
+  constexpr int kHalo = 4 * M;                    // points of the widened range beyond each chunk end
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ unsigned char smem_raw[];
   __shared__ double red[32];
@@ -255,14 +256,13 @@ __global__ void gl1d_cluster_kernel(Gl1dTile t, cpx<R>* __restrict__ u, const cp
       nf1 = F[(int64_t)(2 * s + 4) * rows + r];
     }
     if (!forced(s)) f0 = fh = f1 = zero;
-    // publish the chunk's state, then take the halo's from its owners
-    cpx<R>* pubs = ush + (s & 1) * pub;
-    if (owned) {
-      pubs[j] = us;
-      if (Y != nullptr && s >= t.y_first) Y[(int64_t)s * rows + r] = us;
+    if (owned && Y != nullptr && s >= t.y_first) Y[(int64_t)s * rows + r] = us;
+    if (s % M == 0) {   // publish the chunk's state, then take the halo's from its owners
+      const int b = (s / M) & 1;
+      if (owned) ush[b * pub + j] = us;
+      cluster.sync();
+      if (halo_src != nullptr) us = halo_src[b * pub];
     }
-    cluster.sync();
-    if (halo_src != nullptr) us = halo_src[(s & 1) * pub];
     cpx<R> k = stage(us, f0);
     cpx<R> acc = k;
     k = stage(us + h2 * k, fh);
@@ -270,7 +270,7 @@ __global__ void gl1d_cluster_kernel(Gl1dTile t, cpx<R>* __restrict__ u, const cp
     k = stage(us + h2 * k, fh);
     acc = acc + R(2) * k;
     k = stage(us + h * k, f1);
-    us = owned ? us + h6 * (acc + k) : zero;
+    us = inside ? us + h6 * (acc + k) : zero;   // the halo evolves too until the next exchange
     f0 = f1;
     fh = nfh;
     f1 = nf1;
@@ -608,15 +608,15 @@ cudaError_t launch_ppt(const Gl1dTile& t, int threads, void* u, const void* F, v
 }
 
 // One cluster of CS CTAs per (instance, vector), one point per thread.
-template <typename R, int CS>
+template <typename R, int CS, int M>
 cudaError_t launch_cluster(const Gl1dTile& t, void* u, const void* F, void* Y, double* norms, int* flag,
                            cudaStream_t st) {
   const int chunk = (t.max_n + CS - 1) / CS;
-  const int threads = (chunk + 2 * kHalo + 31) / 32 * 32;   // the widened range of the longest chunk
+  const int threads = (chunk + 8 * M + 31) / 32 * 32;   // the widened range of the longest chunk
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(CS * t.n_inst), (unsigned)t.kg);
   cfg.blockDim = dim3((unsigned)threads);
-  cfg.dynamicSmemBytes = sizeof(cpx<R>) * (2 * (size_t)(threads + 2) + 2 * (size_t)(threads - 2 * kHalo));
+  cfg.dynamicSmemBytes = sizeof(cpx<R>) * (2 * (size_t)(threads + 2) + 2 * (size_t)(threads - 8 * M));
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -625,15 +625,49 @@ cudaError_t launch_cluster(const Gl1dTile& t, void* u, const void* F, void* Y, d
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gl1d_cluster_kernel<R, CS>, t, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y, norms,
+  return cudaLaunchKernelEx(&cfg, gl1d_cluster_kernel<R, CS, M>, t, (cpx<R>*)u, (const cpx<R>*)F, (cpx<R>*)Y, norms,
                             flag);
 }
 
 }  // namespace
 
-// Cluster size for the FP64 RK4 march (0: one CTA per pair): the largest of 8, 4, 2 for which every
-// (instance, vector) pair's cluster fits in one wave and every CTA of the longest instance owns 32 to
-// 256 points.  RSV_GL1D_CLUSTER=0 keeps one CTA per pair.
+// Clusters of 16 CTAs exceed the portable size of 8: taken when the kernel may opt in and the device
+// can hold one (asked once per device; a refusal is cleared so no later call reads it as its own).
+static bool cluster16_ok(int dev) {
+  static std::mutex mu;
+  static int state[64] = {0};   // 0 not asked, 1 yes, 2 no
+  if (dev < 0 || dev >= 64) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  if (state[dev] == 0) {
+    auto kernel = gl1d_cluster_kernel<double, 16, 2>;
+    bool ok = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    if (ok) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(32);
+      cfg.dynamicSmemBytes = sizeof(cpx<double>) * (2 * 34 + 2 * 16);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 16;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      ok = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) == cudaSuccess && clusters > 0;
+    }
+    if (!ok) cudaGetLastError();
+    state[dev] = ok ? 1 : 2;
+  }
+  return state[dev] == 1;
+}
+
+// Cluster size for the FP64 RK4 march (0: one CTA per pair), such that every (instance, vector) pair's
+// cluster fits in one wave.  16 CTAs exchanging every 2 steps when each CTA's chunk and its 8-point
+// halos fill one warp (instances of 128 to 256 points): a cluster barrier per two steps and no second,
+// mostly idle warp, whose FP64 work costs as much as a full one's.  Otherwise the largest of 8, 4, 2
+// for which every CTA of the longest instance owns 32 to 256 points, exchanging every step.
+// RSV_GL1D_CLUSTER=0 keeps one CTA per pair.
 int gl1d_cluster_size(const Gl1dTile& t) {
   static const bool env = [] {
     const char* e = getenv("RSV_GL1D_CLUSTER");
@@ -644,6 +678,7 @@ int gl1d_cluster_size(const Gl1dTile& t) {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
+  if (t.max_n >= 128 && t.max_n <= 256 && (int64_t)t.n_inst * t.kg * 16 <= sms && cluster16_ok(dev)) return 16;
   for (int cs = 8; cs >= 2; cs /= 2)
     if (t.max_n >= 32 * cs && (t.max_n + cs - 1) / cs <= 256 && (int64_t)t.n_inst * t.kg * cs <= sms) return cs;
   return 0;
@@ -658,9 +693,10 @@ cudaError_t launch_gl1d_tile(const Gl1dTile& t, void* u, const void* F, void* Y,
   if (t.max_n > 4096) return cudaErrorInvalidValue;
   if constexpr (sizeof(R) == 8) {   // FP64: spread each march over a cluster of SMs when there are few
     const int cs = gl1d_cluster_size(t);
-    if (cs == 8) return launch_cluster<R, 8>(t, u, F, Y, norms, flag, st);
-    if (cs == 4) return launch_cluster<R, 4>(t, u, F, Y, norms, flag, st);
-    if (cs == 2) return launch_cluster<R, 2>(t, u, F, Y, norms, flag, st);
+    if (cs == 16) return launch_cluster<R, 16, 2>(t, u, F, Y, norms, flag, st);
+    if (cs == 8) return launch_cluster<R, 8, 1>(t, u, F, Y, norms, flag, st);
+    if (cs == 4) return launch_cluster<R, 4, 1>(t, u, F, Y, norms, flag, st);
+    if (cs == 2) return launch_cluster<R, 2, 1>(t, u, F, Y, norms, flag, st);
   }
   const int ppt = t.max_n <= 1024 ? 1 : (t.max_n <= 2048 ? 2 : 4);
   const int threads = (((t.max_n + ppt - 1) / ppt + 31) / 32) * 32;
