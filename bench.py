@@ -243,9 +243,9 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
                  1-D kind (state held on chip for the whole tile): the forcing tile read
                  (2S+1 stage times), the snapshot tile written (S steps) and the state read
                  and written once, (3S + 3) state passes per tile; in FP64 (bound by the FP64
-                 rate, not by bytes) 134 flop per point and step: four evaluations of the
-                 complex three-point stencil and forcing (26 flop each) and the RK4 combination
-                 (three stage inputs and three accumulations at 4 flop, the update at 6);
+                 rate, not by bytes) 122 flop per point and step: four evaluations of
+                 k = A x + f (three complex multiply-adds, 24 flop), the three stage inputs
+                 u + c k (4 flop each) and the update u + h/6 (k1 + 2 k2 + 2 k3 + k4) (14 flop);
                  2-D whole-step kernel: 6 state passes per step (state read and written,
                  forcing read at the three stage times, snapshot written);
                  per-stage and stage-pair kernels (2-D, 3-D): 15 state passes per step, the
@@ -290,7 +290,7 @@ def kernel_model(cat, w, prec, tile, groups, ms_total, rows, path):
         bound, unit, peak, per = "hbm", "GB/s", peaks["hbm_gbs"], 1e9
         src = peaks["src"] + " copy bandwidth"
     elif cat == "march" and "kind=gl1d" in path and prec == "fp64":
-        work = 134.0 * rows * S
+        work = 122.0 * rows * S
         bound, unit, peak, per = "alu", "TFLOP/s", FP64_ALU_TFLOPS, 1e12
         src = "nominal FP64"
     elif cat == "march" and "kind=gl1d" in path:
