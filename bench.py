@@ -230,6 +230,7 @@ TRAFFIC = {
 }
 
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+REF_TOTAL_S = 150.0                                   # CPU seconds of the reference arm's timed steps
 FP64_ALU_TFLOPS = 1.25                                # nominal FP64 rate of the part
 
 
@@ -708,7 +709,10 @@ def run_reference(args):
     name = args.workload
     w = workload(name)
     t0 = time.perf_counter()
-    last = cpu_baseline(name, target_seconds=args.ref_seconds, warmup=args.warmup, repeats=max(1, args.steps))
+    # each step's sample: about --ref-seconds of CPU work, less when the K steps would exceed about
+    # REF_TOTAL_S in all (never less than one step of the workload)
+    per_step_s = min(args.ref_seconds, REF_TOTAL_S / max(1, args.steps))
+    last = cpu_baseline(name, target_seconds=per_step_s, warmup=args.warmup, repeats=max(1, args.steps))
     wall = time.perf_counter() - t0
     vals = last.get("samples") or []
     v = statistics.median(vals) if vals else None
